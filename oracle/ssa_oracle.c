@@ -1,0 +1,777 @@
+/*
+ * ssa_oracle.c -- reference implementation of the reduced-precision Gillespie
+ * direct method (Kimpson, Flegg & Flegg, "Reduced-Precision Stochastic
+ * Simulation for Mathematical Biology").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle: a plain, slow,
+ * single-threaded CPU implementation written from the paper.  Only the tests,
+ * the smoke check and the benchmark's CPU-baseline leg may load it.  It shares
+ * no code, header, table or constant generator with the CUDA engine in
+ * paper_2605_00479_gb300/csrc; the two are written independently and agree
+ * only because both follow the arithmetic contract spelled out below.
+ *
+ * Build: gcc -std=c11 -O2 -ffp-contract=off -fno-fast-math -shared -fPIC.
+ * No fused multiply-add is allowed: every operation below is one IEEE-754
+ * binary32/binary64 operation in round-to-nearest-even.
+ *
+ * Paper passages followed (section / equation / table of the paper):
+ *   - Direct method steps 1-4 (Sec. 2, "In the Direct Method formulation"):
+ *       propensities and a0, tau = -ln(u1)/a0, smallest mu with
+ *       sum_{j<=mu} a_j > u2*a0, x += nu_mu, t += tau.
+ *   - Precision partition (Sec. 3.2 "Mixed-precision partitioning", Sec. 4
+ *     mode list): FP64, FP32, mixed (16-bit propensities, fp32 sum and time,
+ *     integer state), uniform (every operation in the 16-bit type).
+ *   - Formats (Table "formats"): binary16 = 1/5/10 bits, bfloat16 = 1/8/7.
+ *   - Stochastic rounding (Sec. 3.3, SR equation): round up with probability
+ *     (x - x-)/(x+ - x-); applied after every arithmetic operation whose result
+ *     type is the 16-bit type ("every-op" SR, Sec. 3.3).
+ *   - Propensity forms: mass action with combinatorial factors (Sec. 4.2
+ *     Schloegl k2 n(n-1)(n-2); Sec. 4.4 dimer kf nA(nA-1)/2) and Hill
+ *     repression alpha0 + alpha/(1+P^h) (Sec. 4.5).
+ *   - Propensity normalisation (Sec. 4.2, rescaled Schloegl): reservoir
+ *     (constant) species are folded into the rate constant, k1*A and k3*B.
+ *
+ * Where the paper is silent the readings below are used (each one also listed
+ * in the design notes):
+ *   R1 rate constants are Gillespie c-constants; c'_j = c_j / prod_i r_ij!,
+ *      computed in binary64, then (normalise) multiplied by the falling
+ *      factorials of the constant species' counts, species ascending,
+ *      factor m = 0..r-1 ascending.  c'_j is converted to the propensity type
+ *      once, by round-to-nearest (binary64 -> binary32 -> 16-bit).
+ *   R2 time in mixed mode is binary32 (Sec. 4 mode list).
+ *   R3 propensity op order: a = c'; for each reactant species i ascending, for
+ *      m = 0..r_ij-1: f = rnd(x_i - m); a = rnd(a * f).  Zero when any
+ *      x_i < r_ij (no operations, but the step's random-bit schedule is fixed).
+ *      Hill: P = rnd(x_reg); q = P; (h-1) times q = rnd(q*P); d = rnd(1 + q);
+ *      f = rnd(alpha / d); a = rnd(alpha0 + f).
+ *   R4 a 16-bit operation is the binary32 operation on the widened operands
+ *      followed by one rounding to the 16-bit type.
+ *   R5 SR rounding bits: each SR operation consumes one 16-bit random value.
+ *      bfloat16: add the 16 bits to the 16 discarded bits of the binary32
+ *      pattern and truncate.  binary16: add the low 13 bits, aligned with the
+ *      most significant discarded bit, and truncate (13 bits of rounding
+ *      resolution).  Overflow past the largest finite value gives infinity.
+ *   R6 random numbers: Philox4x32-10 with key = (seed lo, seed hi) and
+ *      counter = (block lo, block hi, trajectory id, stream).  Each trajectory
+ *      reads two streams of 32-bit words (word w is lane w mod 4 of block w/4).
+ *      Stream 0 holds the uniforms: step n takes words 2n and 2n+1,
+ *      u1 = (w0 + 1) 2^-32 in (0,1] and u2 = w1 2^-32 in [0,1) in FP64 mode,
+ *      u1 = ((w0 >> 8) + 1) 2^-24 and u2 = (w1 >> 8) 2^-24 otherwise, so every
+ *      mode sees the same draws (common random numbers).  Stream 1 holds the
+ *      SR bits: with S rounding operations per step, step n owns words
+ *      [n*ceil(S/2), (n+1)*ceil(S/2)) and operation i takes the low (even i) or
+ *      high (odd i) half of word i/2.  RN modes never read stream 1.
+ *   R7 uniform mode: E = rnd(-log(u1)) with log evaluated in binary32 on u1,
+ *      U2 = rnd(u2), tau = rnd(E / a0), target = rnd(U2 * a0),
+ *      t_new = rnd(t + tau).  SR operation order within a step: propensity
+ *      chains (reaction order), partial sums S_1..S_{M-1}, E, U2, tau,
+ *      target, t_new.
+ *   R8 log: own implementation, ln x = e ln2 + 2 atanh(s), s = (m-1)/(m+1),
+ *      m in [sqrt(1/2), sqrt(2)], odd atanh series to s^9 (binary32) or s^23
+ *      (binary64), Cody-Waite split of ln2, Horner order fixed below.
+ *   R9 degenerate steps: a0 == 0 ends the trajectory (absorbing state);
+ *      a0 = inf -> status OVERFLOW; a0 = NaN -> status NAN; n >= max_events
+ *      -> status MAX_EVENTS; a negative count after an update -> status
+ *      STATE_RANGE; remaining snapshots are filled with the current state.
+ *      If no partial sum exceeds the target, the last reaction with a_j > 0
+ *      fires.
+ *   R10 snapshot k receives the state after every event with event time
+ *      <= s_k: before an event at t_new is applied, all s_k < t_new are
+ *      written.  Sample times and t_end are rounded to the time type by RN.
+ */
+#include <stdint.h>
+#include <string.h>
+#include <stdlib.h>
+
+/* ------------------------------------------------------------------------ */
+/* Bit access                                                                */
+/* ------------------------------------------------------------------------ */
+static uint32_t f2u(float x) { uint32_t u; memcpy(&u, &x, 4); return u; }
+static float u2f(uint32_t u) { float x; memcpy(&x, &u, 4); return x; }
+static uint64_t d2u(double x) { uint64_t u; memcpy(&u, &x, 8); return u; }
+static double u2d(uint64_t u) { double x; memcpy(&x, &u, 8); return x; }
+
+static int f32_is_nan(float x) { return (f2u(x) & 0x7FFFFFFFu) > 0x7F800000u; }
+static int f32_is_inf(float x) { return (f2u(x) & 0x7FFFFFFFu) == 0x7F800000u; }
+static int f64_is_nan(double x) { return (d2u(x) & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull; }
+static int f64_is_inf(double x) { return (d2u(x) & 0x7FFFFFFFFFFFFFFFull) == 0x7FF0000000000000ull; }
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the     */
+/* multiply-xor bijection on a 128-bit counter with a 64-bit key that is      */
+/* bumped by the Weyl constants between rounds.                               */
+/* ------------------------------------------------------------------------ */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+typedef struct {
+    uint32_t key[2];
+    uint32_t traj;          /* global trajectory id */
+    uint32_t stream;        /* 0: uniforms, 1: stochastic-rounding bits */
+    uint64_t block;         /* index of the block held in buf */
+    int have;
+    uint32_t buf[4];
+} word_stream;
+
+static uint32_t stream_word(word_stream *s, uint64_t w)
+{
+    uint64_t b = w >> 2;
+    if (!s->have || b != s->block) {
+        uint32_t ctr[4];
+        ctr[0] = (uint32_t)b;
+        ctr[1] = (uint32_t)(b >> 32);
+        ctr[2] = s->traj;
+        ctr[3] = s->stream;
+        oracle_philox4x32_10(ctr, s->key, s->buf);
+        s->block = b;
+        s->have = 1;
+    }
+    return s->buf[w & 3];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Natural logarithm (reading R8).  x = 2^e * m with m in [sqrt(1/2),sqrt(2)],*/
+/* ln m = 2 atanh(s), s = (m - 1)/(m + 1), atanh s = s + s^3/3 + s^5/5 + ...  */
+/* ln 2 = LN2_HI + LN2_LO with LN2_HI holding the leading 16 (binary32) or    */
+/* 32 (binary64) bits of ln 2, so that e * LN2_HI is exact.                    */
+/* Domain: positive normal numbers (the uniforms used are >= 2^-53).          */
+/* ------------------------------------------------------------------------ */
+float oracle_log_f32(float x)
+{
+    const float LN2_HI = 0x1.62e400p-1f;
+    const float LN2_LO = 0x1.7f7d1cp-20f;
+    uint32_t u = f2u(x);
+    int e = (int)(u >> 23) - 127;
+    uint32_t mb = (u & 0x7FFFFFu) | 0x3F800000u;      /* m in [1, 2) */
+    if (mb > 0x3FB504F3u) {                             /* m > sqrt(2): halve it */
+        mb -= 0x00800000u;
+        e += 1;
+    }
+    float m = u2f(mb);
+    float f = m - 1.0f;
+    float d = m + 1.0f;
+    float s = f / d;
+    float z = s * s;
+    /* 2 atanh(s) = 2s + s z (2/3 + z (2/5 + z (2/7 + z 2/9))) */
+    float p = 2.0f / 9.0f;
+    p = z * p;  p = (2.0f / 7.0f) + p;
+    p = z * p;  p = (2.0f / 5.0f) + p;
+    p = z * p;  p = (2.0f / 3.0f) + p;
+    float r = s * z;
+    r = r * p;
+    float two_s = s + s;
+    r = two_s + r;
+    float ef = (float)e;
+    float lo = ef * LN2_LO;
+    lo = lo + r;
+    float hi = ef * LN2_HI;
+    return hi + lo;
+}
+
+double oracle_log_f64(double x)
+{
+    const double LN2_HI = 0x1.62e42fee00000p-1;
+    const double LN2_LO = 0x1.a39ef35793c76p-33;
+    uint64_t u = d2u(x);
+    int e = (int)(u >> 52) - 1023;
+    uint64_t mb = (u & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    if (mb > 0x3FF6A09E667F3BCCull) {                  /* m > sqrt(2) */
+        mb -= 0x0010000000000000ull;
+        e += 1;
+    }
+    double m = u2d(mb);
+    double f = m - 1.0;
+    double d = m + 1.0;
+    double s = f / d;
+    double z = s * s;
+    /* coefficients 2/(2k+1), k = 1..11, evaluated by Horner from the top */
+    double p = 2.0 / 23.0;
+    p = z * p;  p = (2.0 / 21.0) + p;
+    p = z * p;  p = (2.0 / 19.0) + p;
+    p = z * p;  p = (2.0 / 17.0) + p;
+    p = z * p;  p = (2.0 / 15.0) + p;
+    p = z * p;  p = (2.0 / 13.0) + p;
+    p = z * p;  p = (2.0 / 11.0) + p;
+    p = z * p;  p = (2.0 / 9.0) + p;
+    p = z * p;  p = (2.0 / 7.0) + p;
+    p = z * p;  p = (2.0 / 5.0) + p;
+    p = z * p;  p = (2.0 / 3.0) + p;
+    double r = s * z;
+    r = r * p;
+    double two_s = s + s;
+    r = two_s + r;
+    double ef = (double)e;
+    double lo = ef * LN2_LO;
+    lo = lo + r;
+    double hi = ef * LN2_HI;
+    return hi + lo;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 16-bit formats.  binary16: 1 sign, 5 exponent (bias 15), 10 fraction bits, */
+/* subnormal quantum 2^-24, largest finite 65504.  bfloat16: the upper 16     */
+/* bits of a binary32 pattern.                                                 */
+/* ------------------------------------------------------------------------ */
+float oracle_f16_to_f32(uint16_t h)
+{
+    uint32_t sign = (uint32_t)(h >> 15) << 31;
+    uint32_t e = (h >> 10) & 0x1Fu;
+    uint32_t m = h & 0x3FFu;
+    if (e == 31) return u2f(sign | 0x7F800000u | (m << 13));
+    if (e == 0) {
+        float v = (float)m * 0x1p-24f;                  /* exact */
+        return (sign ? -v : v);
+    }
+    return u2f(sign | ((e - 15 + 127) << 23) | (m << 13));
+}
+
+float oracle_bf16_to_f32(uint16_t b) { return u2f((uint32_t)b << 16); }
+
+/* binary32 -> binary16.  sr == 0: round to nearest, ties to even.
+ * sr != 0: stochastic rounding with the low 13 bits of r (reading R5). */
+uint16_t oracle_f32_to_f16(float x, int sr, uint32_t r)
+{
+    uint32_t u = f2u(x);
+    uint16_t sign = (uint16_t)((u >> 16) & 0x8000u);
+    uint32_t a = u & 0x7FFFFFFFu;
+    if (a > 0x7F800000u) return sign | 0x7E00u;        /* NaN */
+    if (a == 0x7F800000u) return sign | 0x7C00u;       /* infinity */
+    if (a == 0) return sign;
+    int be = (int)(a >> 23);
+    uint64_t sig = (a & 0x7FFFFFu) | (be ? 0x800000u : 0u);
+    int ex = be ? be - 150 : -149;                      /* |x| = sig * 2^ex */
+    int E = be ? be - 127 : -126;
+    if (E > 15) return sign | 0x7C00u;                  /* >= 2^16: beyond binary16 */
+    int q = (E >= -14) ? E - 10 : -24;                  /* exponent of the binary16 quantum */
+    int k = q - ex;                                     /* discarded bits, >= 13 */
+    uint64_t n;
+    if (!sr) {
+        if (k > 40) {
+            n = 0;                                       /* below half a quantum */
+        } else {
+            uint64_t one = 1;
+            n = sig >> k;
+            uint64_t rem = sig & ((one << k) - 1);
+            uint64_t half = one << (k - 1);
+            if (rem > half || (rem == half && (n & 1))) n += 1;
+        }
+    } else {
+        if (k > 36) {
+            n = 0;                                       /* sig + r13*2^(k-13) < 2^k */
+        } else {
+            uint64_t add = (uint64_t)(r & 0x1FFFu) << (k - 13);
+            n = (sig + add) >> k;
+        }
+    }
+    uint32_t hb;
+    if (q == -24) hb = (uint32_t)n;                     /* n == 1024 encodes 2^-14 */
+    else hb = ((uint32_t)(E + 15) << 10) + (uint32_t)(n - 1024);
+    if (hb >= 0x7C00u) hb = 0x7C00u;
+    return sign | (uint16_t)hb;
+}
+
+/* binary32 -> bfloat16.  sr == 0: round to nearest even.  sr != 0: add the
+ * low 16 bits of r to the discarded half and truncate (reading R5). */
+uint16_t oracle_f32_to_bf16(float x, int sr, uint32_t r)
+{
+    uint32_t u = f2u(x);
+    uint16_t sign = (uint16_t)((u >> 16) & 0x8000u);
+    uint32_t a = u & 0x7FFFFFFFu;
+    if (a > 0x7F800000u) return sign | 0x7FC0u;
+    if (a == 0x7F800000u) return sign | 0x7F80u;
+    uint32_t n;
+    if (!sr) {
+        n = a >> 16;
+        uint32_t rem = a & 0xFFFFu;
+        if (rem > 0x8000u || (rem == 0x8000u && (n & 1u))) n += 1;
+    } else {
+        n = (a + (r & 0xFFFFu)) >> 16;
+    }
+    if (n >= 0x7F80u) n = 0x7F80u;
+    return sign | (uint16_t)n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Model and run parameters                                                  */
+/* ------------------------------------------------------------------------ */
+enum { P_FP64 = 0, P_FP32 = 1, P_MIXED_F16 = 2, P_MIXED_BF16 = 3, P_UNIFORM_F16 = 4, P_UNIFORM_BF16 = 5 };
+enum { LAW_MASS_ACTION = 0, LAW_HILL = 1 };
+enum { ST_OVERFLOW = 1, ST_MAX_EVENTS = 2, ST_STATE_RANGE = 4, ST_NAN = 8 };
+
+#define OR_MAX_N 64
+#define OR_MAX_M 64
+
+typedef struct {
+    int N, M;
+    const int32_t *order;     /* [M][N] */
+    const int32_t *stoich;    /* [M][N] */
+    const int32_t *law;       /* [M] */
+    const double *hill;       /* [M][4] alpha0, alpha, h, regulator */
+    const uint8_t *constant;  /* [N] */
+    int normalise;
+    double cprime[OR_MAX_M];  /* R1, binary64 */
+    int folded[OR_MAX_M][OR_MAX_N];  /* 1: factor moved into cprime */
+} omodel;
+
+/* ------------------------------------------------------------------------ */
+/* Rounding context: which 16-bit format, RN or SR, and where this step's SR  */
+/* values live in the trajectory's word stream.                              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int bf16;          /* 0: binary16, 1: bfloat16 */
+    int sr;
+    word_stream *ws;
+    uint64_t sr_base;  /* first SR word of the current step */
+    int op;            /* SR operation index within the step */
+} rounder;
+
+/* Round a binary32 value to the 16-bit type; return it widened (exact). */
+static float rnd16(rounder *R, float x)
+{
+    uint32_t r = 0;
+    if (R->sr) {
+        uint32_t w = stream_word(R->ws, R->sr_base + (uint64_t)(R->op >> 1));
+        r = (R->op & 1) ? (w >> 16) : (w & 0xFFFFu);
+    }
+    R->op += 1;
+    if (R->bf16) return oracle_bf16_to_f32(oracle_f32_to_bf16(x, R->sr, r));
+    return oracle_f16_to_f32(oracle_f32_to_f16(x, R->sr, r));
+}
+
+/* round to the 16-bit type by RN without consuming an SR slot (constants) */
+static float rn16(int bf16, float x)
+{
+    if (bf16) return oracle_bf16_to_f32(oracle_f32_to_bf16(x, 0, 0));
+    return oracle_f16_to_f32(oracle_f32_to_f16(x, 0, 0));
+}
+
+static double factorial(int r)
+{
+    double f = 1.0;
+    for (int i = 2; i <= r; ++i) f = f * (double)i;
+    return f;
+}
+
+/* number of 16-bit rounding operations in the propensity chain of reaction j */
+static int chain_ops(const omodel *md, int j)
+{
+    if (md->law[j] == LAW_HILL) return (int)md->hill[4 * j + 2] + 3;
+    int ops = 0;
+    for (int i = 0; i < md->N; ++i)
+        if (!md->folded[j][i]) ops += 2 * md->order[j * md->N + i];
+    return ops;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Propensities per precision family (reading R3)                            */
+/* ------------------------------------------------------------------------ */
+static int reactants_short(const omodel *md, int j, const int32_t *x)
+{
+    for (int i = 0; i < md->N; ++i) {
+        int r = md->order[j * md->N + i];
+        if (r > 0 && !md->folded[j][i] && x[i] < r) return 1;
+    }
+    return 0;
+}
+
+static double prop_f64(const omodel *md, int j, const int32_t *x, const double *cp, const double *h0, const double *h1)
+{
+    if (md->law[j] == LAW_HILL) {
+        int hh = (int)md->hill[4 * j + 2];
+        int reg = (int)md->hill[4 * j + 3];
+        double P = (double)x[reg];
+        double q = P;
+        for (int m = 1; m < hh; ++m) q = q * P;
+        double d = 1.0 + q;
+        double f = h1[j] / d;
+        return h0[j] + f;
+    }
+    if (reactants_short(md, j, x)) return 0.0;
+    double a = cp[j];
+    for (int i = 0; i < md->N; ++i) {
+        if (md->folded[j][i]) continue;
+        for (int m = 0; m < md->order[j * md->N + i]; ++m) a = a * (double)(x[i] - m);
+    }
+    return a;
+}
+
+static float prop_f32(const omodel *md, int j, const int32_t *x, const float *cp, const float *h0, const float *h1)
+{
+    if (md->law[j] == LAW_HILL) {
+        int hh = (int)md->hill[4 * j + 2];
+        int reg = (int)md->hill[4 * j + 3];
+        float P = (float)x[reg];
+        float q = P;
+        for (int m = 1; m < hh; ++m) q = q * P;
+        float d = 1.0f + q;
+        float f = h1[j] / d;
+        return h0[j] + f;
+    }
+    if (reactants_short(md, j, x)) return 0.0f;
+    float a = cp[j];
+    for (int i = 0; i < md->N; ++i) {
+        if (md->folded[j][i]) continue;
+        for (int m = 0; m < md->order[j * md->N + i]; ++m) a = a * (float)(x[i] - m);
+    }
+    return a;
+}
+
+/* 16-bit propensity; R->op must point at this reaction's first SR slot */
+static float prop_16(const omodel *md, int j, const int32_t *x, const float *cp, const float *h0, const float *h1, rounder *R)
+{
+    int op_end = R->op + chain_ops(md, j);
+    float a;
+    if (md->law[j] == LAW_HILL) {
+        int hh = (int)md->hill[4 * j + 2];
+        int reg = (int)md->hill[4 * j + 3];
+        float P = rnd16(R, (float)x[reg]);
+        float q = P;
+        for (int m = 1; m < hh; ++m) q = rnd16(R, q * P);
+        float d = rnd16(R, 1.0f + q);
+        float f = rnd16(R, h1[j] / d);
+        a = rnd16(R, h0[j] + f);
+    } else if (reactants_short(md, j, x)) {
+        a = 0.0f;
+    } else {
+        a = cp[j];
+        for (int i = 0; i < md->N; ++i) {
+            if (md->folded[j][i]) continue;
+            for (int m = 0; m < md->order[j * md->N + i]; ++m) {
+                float f = rnd16(R, (float)(x[i] - m));
+                a = rnd16(R, a * f);
+            }
+        }
+    }
+    R->op = op_end;  /* the schedule is fixed even when the chain was skipped */
+    return a;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Output helpers                                                             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    void *out;
+    int state_bytes;
+    int64_t n_traj;
+    int64_t col;
+    int K, N;
+} sink;
+
+static void write_snapshot(const sink *S, int k, const int32_t *x, uint32_t *status)
+{
+    for (int i = 0; i < S->N; ++i) {
+        int64_t idx = ((int64_t)k * S->N + i) * S->n_traj + S->col;
+        if (S->state_bytes == 2) {
+            int32_t v = x[i];
+            if (v > 32767) { v = 32767; *status |= ST_STATE_RANGE; }
+            if (v < -32768) { v = -32768; *status |= ST_STATE_RANGE; }
+            ((int16_t *)S->out)[idx] = (int16_t)v;
+        } else {
+            ((int32_t *)S->out)[idx] = x[i];
+        }
+    }
+}
+
+static void apply_event(const omodel *md, int mu, int32_t *x, uint32_t *status)
+{
+    for (int i = 0; i < md->N; ++i) {
+        if (md->constant && md->constant[i]) continue;
+        x[i] += md->stoich[mu * md->N + i];
+        if (x[i] < 0) *status |= ST_STATE_RANGE;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One trajectory per precision family                                        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double t_end;
+    int K;
+    const double *samples;
+    int64_t max_events;
+} runp;
+
+static void traj_f64(const omodel *md, const runp *rp, word_stream *ws, int32_t *x,
+                     const sink *S, uint32_t *status, int64_t *n_events, double *t_final)
+{
+    const int M = md->M;
+    double cp[OR_MAX_M], h0[OR_MAX_M], h1[OR_MAX_M], a[OR_MAX_M], Ssum[OR_MAX_M];
+    for (int j = 0; j < M; ++j) {
+        cp[j] = md->cprime[j];
+        h0[j] = md->law[j] == LAW_HILL ? md->hill[4 * j] : 0.0;
+        h1[j] = md->law[j] == LAW_HILL ? md->hill[4 * j + 1] : 0.0;
+    }
+    double t = 0.0;
+    int64_t n = 0;
+    int k = 0;
+    for (;;) {
+        if (n >= rp->max_events) { *status |= ST_MAX_EVENTS; break; }
+        for (int j = 0; j < M; ++j) a[j] = prop_f64(md, j, x, cp, h0, h1);
+        Ssum[0] = a[0];
+        for (int j = 1; j < M; ++j) Ssum[j] = Ssum[j - 1] + a[j];
+        double a0 = Ssum[M - 1];
+        if (f64_is_nan(a0)) { *status |= ST_NAN; break; }
+        if (f64_is_inf(a0)) { *status |= ST_OVERFLOW; break; }
+        if (a0 == 0.0) break;
+        uint64_t w = (uint64_t)n * 2u;
+        uint32_t w0 = stream_word(ws, w), w1 = stream_word(ws, w + 1);
+        double u1 = ((double)w0 + 1.0) * 0x1p-32;
+        double u2 = (double)w1 * 0x1p-32;
+        double E = -oracle_log_f64(u1);
+        double tau = E / a0;
+        double target = u2 * a0;
+        double t_new = t + tau;
+        while (k < rp->K && rp->samples[k] < t_new) write_snapshot(S, k++, x, status);
+        if (t_new > rp->t_end) break;
+        int mu = -1;
+        for (int j = 0; j < M; ++j) if (Ssum[j] > target) { mu = j; break; }
+        if (mu < 0) for (int j = M - 1; j >= 0; --j) if (a[j] > 0.0) { mu = j; break; }
+        apply_event(md, mu, x, status);
+        t = t_new;
+        n += 1;
+        if (*status & ST_STATE_RANGE) break;
+    }
+    while (k < rp->K) write_snapshot(S, k++, x, status);
+    *n_events = n;
+    *t_final = t;
+}
+
+/* FP32 mode (bf16 < 0) and mixed modes (bf16 = 0 binary16, 1 bfloat16) */
+static void traj_f32_mixed(const omodel *md, const runp *rp, word_stream *ws, word_stream *wsr, int32_t *x,
+                           const sink *S, uint32_t *status, int64_t *n_events, double *t_final,
+                           int fmt, int sr)
+{
+    const int M = md->M;
+    const int mixed = fmt >= 0;
+    float cp[OR_MAX_M], h0[OR_MAX_M], h1[OR_MAX_M], a[OR_MAX_M], Ssum[OR_MAX_M];
+    int nsr = 0;
+    for (int j = 0; j < M; ++j) {
+        float c = (float)md->cprime[j];
+        float g0 = md->law[j] == LAW_HILL ? (float)md->hill[4 * j] : 0.0f;
+        float g1 = md->law[j] == LAW_HILL ? (float)md->hill[4 * j + 1] : 0.0f;
+        if (mixed) { c = rn16(fmt, c); g0 = rn16(fmt, g0); g1 = rn16(fmt, g1); }
+        cp[j] = c; h0[j] = g0; h1[j] = g1;
+        if (mixed && sr) nsr += chain_ops(md, j);
+    }
+    const uint64_t Ws = (uint64_t)((nsr + 1) / 2);   /* SR words per step */
+    float t_end = (float)rp->t_end;
+    float smp[1024];
+    for (int kk = 0; kk < rp->K; ++kk) smp[kk] = (float)rp->samples[kk];
+    rounder R;
+    R.bf16 = fmt; R.sr = sr; R.ws = wsr; R.sr_base = 0; R.op = 0;
+    float t = 0.0f;
+    int64_t n = 0;
+    int k = 0;
+    for (;;) {
+        if (n >= rp->max_events) { *status |= ST_MAX_EVENTS; break; }
+        uint64_t w = (uint64_t)n * 2u;
+        R.sr_base = (uint64_t)n * Ws;
+        R.op = 0;
+        for (int j = 0; j < M; ++j)
+            a[j] = mixed ? prop_16(md, j, x, cp, h0, h1, &R) : prop_f32(md, j, x, cp, h0, h1);
+        Ssum[0] = a[0];
+        for (int j = 1; j < M; ++j) Ssum[j] = Ssum[j - 1] + a[j];
+        float a0 = Ssum[M - 1];
+        if (f32_is_nan(a0)) { *status |= ST_NAN; break; }
+        if (f32_is_inf(a0)) { *status |= ST_OVERFLOW; break; }
+        if (a0 == 0.0f) break;
+        uint32_t w0 = stream_word(ws, w), w1 = stream_word(ws, w + 1);
+        float u1 = (float)((w0 >> 8) + 1u) * 0x1p-24f;
+        float u2 = (float)(w1 >> 8) * 0x1p-24f;
+        float E = -oracle_log_f32(u1);
+        float tau = E / a0;
+        float target = u2 * a0;
+        float t_new = t + tau;
+        while (k < rp->K && smp[k] < t_new) write_snapshot(S, k++, x, status);
+        if (t_new > t_end) break;
+        int mu = -1;
+        for (int j = 0; j < M; ++j) if (Ssum[j] > target) { mu = j; break; }
+        if (mu < 0) for (int j = M - 1; j >= 0; --j) if (a[j] > 0.0f) { mu = j; break; }
+        apply_event(md, mu, x, status);
+        t = t_new;
+        n += 1;
+        if (*status & ST_STATE_RANGE) break;
+    }
+    while (k < rp->K) write_snapshot(S, k++, x, status);
+    *n_events = n;
+    *t_final = (double)t;
+}
+
+static void traj_uniform(const omodel *md, const runp *rp, word_stream *ws, word_stream *wsr, int32_t *x,
+                         const sink *S, uint32_t *status, int64_t *n_events, double *t_final,
+                         int fmt, int sr)
+{
+    const int M = md->M;
+    float cp[OR_MAX_M], h0[OR_MAX_M], h1[OR_MAX_M], a[OR_MAX_M], Ssum[OR_MAX_M];
+    int nsr = 0;
+    for (int j = 0; j < M; ++j) {
+        cp[j] = rn16(fmt, (float)md->cprime[j]);
+        h0[j] = md->law[j] == LAW_HILL ? rn16(fmt, (float)md->hill[4 * j]) : 0.0f;
+        h1[j] = md->law[j] == LAW_HILL ? rn16(fmt, (float)md->hill[4 * j + 1]) : 0.0f;
+        nsr += chain_ops(md, j);
+    }
+    nsr += (M - 1) + 5;   /* partial sums, E, U2, tau, target, t_new */
+    const uint64_t Ws = (uint64_t)((nsr + 1) / 2);   /* SR words per step */
+    float t_end = rn16(fmt, (float)rp->t_end);
+    float smp[1024];
+    for (int kk = 0; kk < rp->K; ++kk) smp[kk] = rn16(fmt, (float)rp->samples[kk]);
+    rounder R;
+    R.bf16 = fmt; R.sr = sr; R.ws = wsr; R.sr_base = 0; R.op = 0;
+    float t = 0.0f;
+    int64_t n = 0;
+    int k = 0;
+    for (;;) {
+        if (n >= rp->max_events) { *status |= ST_MAX_EVENTS; break; }
+        uint64_t w = (uint64_t)n * 2u;
+        R.sr_base = (uint64_t)n * Ws;
+        R.op = 0;
+        for (int j = 0; j < M; ++j) a[j] = prop_16(md, j, x, cp, h0, h1, &R);
+        Ssum[0] = a[0];
+        for (int j = 1; j < M; ++j) Ssum[j] = rnd16(&R, Ssum[j - 1] + a[j]);
+        float a0 = Ssum[M - 1];
+        if (f32_is_nan(a0)) { *status |= ST_NAN; break; }
+        if (f32_is_inf(a0)) { *status |= ST_OVERFLOW; break; }
+        if (a0 == 0.0f) break;
+        uint32_t w0 = stream_word(ws, w), w1 = stream_word(ws, w + 1);
+        float u1 = (float)((w0 >> 8) + 1u) * 0x1p-24f;
+        float u2 = (float)(w1 >> 8) * 0x1p-24f;
+        float E = rnd16(&R, -oracle_log_f32(u1));
+        float U2 = rnd16(&R, u2);
+        float tau = rnd16(&R, E / a0);
+        float target = rnd16(&R, U2 * a0);
+        float t_new = rnd16(&R, t + tau);
+        while (k < rp->K && smp[k] < t_new) write_snapshot(S, k++, x, status);
+        if (t_new > t_end) break;
+        int mu = -1;
+        for (int j = 0; j < M; ++j) if (Ssum[j] > target) { mu = j; break; }
+        if (mu < 0) for (int j = M - 1; j >= 0; --j) if (a[j] > 0.0f) { mu = j; break; }
+        apply_event(md, mu, x, status);
+        t = t_new;
+        n += 1;
+        if (*status & ST_STATE_RANGE) break;
+    }
+    while (k < rp->K) write_snapshot(S, k++, x, status);
+    *n_events = n;
+    *t_final = (double)t;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public entry: simulate trajectories g0 .. g0+n_traj-1.  Returns 0 on        */
+/* success, -1 on invalid arguments.                                           */
+/* Snapshots: out[(k*N + i)*n_traj + r] (int32 or int16 per state_bytes).     */
+/* ------------------------------------------------------------------------ */
+int oracle_run(int N, int M, const int32_t *order, const int32_t *stoich, const double *rate,
+               const int32_t *law, const double *hill, const uint8_t *constant,
+               const int32_t *x0, int64_t n_traj, uint64_t g0, double t_end,
+               int K, const double *samples, int precision, int rounding, int normalise,
+               uint64_t seed, int64_t max_events, int state_bytes,
+               void *out, uint32_t *status, int64_t *n_events, double *t_final)
+{
+    if (N < 1 || N > OR_MAX_N || M < 1 || M > OR_MAX_M || K < 0 || K > 1024) return -1;
+    if (precision < 0 || precision > 5 || rounding < 0 || rounding > 1) return -1;
+    if (rounding == 1 && precision < 2) return -1;
+    if (state_bytes != 2 && state_bytes != 4) return -1;
+    if (n_traj < 0 || g0 + (uint64_t)n_traj > 0x100000000ull) return -1;  /* 32-bit trajectory ids */
+    omodel md;
+    memset(&md, 0, sizeof(md));
+    md.N = N; md.M = M; md.order = order; md.stoich = stoich; md.law = law;
+    md.hill = hill; md.constant = constant; md.normalise = normalise;
+    for (int j = 0; j < M; ++j) {
+        if (law[j] == LAW_HILL) { md.cprime[j] = 0.0; continue; }
+        double denom = 1.0;
+        for (int i = 0; i < N; ++i) denom = denom * factorial(order[j * N + i]);
+        double c = rate[j] / denom;
+        if (normalise && constant) {
+            for (int i = 0; i < N; ++i) {
+                if (!constant[i] || order[j * N + i] == 0) continue;
+                for (int m = 0; m < order[j * N + i]; ++m) c = c * (double)(x0[i] - m);
+                md.folded[j][i] = 1;
+            }
+        }
+        md.cprime[j] = c;
+    }
+    runp rp;
+    rp.t_end = t_end; rp.K = K; rp.samples = samples; rp.max_events = max_events;
+    for (int64_t r = 0; r < n_traj; ++r) {
+        word_stream ws, wsr;
+        memset(&ws, 0, sizeof(ws));
+        ws.key[0] = (uint32_t)seed;
+        ws.key[1] = (uint32_t)(seed >> 32);
+        ws.traj = (uint32_t)(g0 + (uint64_t)r);
+        ws.stream = 0;
+        wsr = ws;
+        wsr.stream = 1;
+        int32_t x[OR_MAX_N];
+        for (int i = 0; i < N; ++i) x[i] = x0[i];
+        sink S;
+        S.out = out; S.state_bytes = state_bytes; S.n_traj = n_traj; S.col = r; S.K = K; S.N = N;
+        uint32_t st = 0;
+        int64_t ne = 0;
+        double tf = 0.0;
+        switch (precision) {
+        case P_FP64: traj_f64(&md, &rp, &ws, x, &S, &st, &ne, &tf); break;
+        case P_FP32: traj_f32_mixed(&md, &rp, &ws, &wsr, x, &S, &st, &ne, &tf, -1, 0); break;
+        case P_MIXED_F16: traj_f32_mixed(&md, &rp, &ws, &wsr, x, &S, &st, &ne, &tf, 0, rounding); break;
+        case P_MIXED_BF16: traj_f32_mixed(&md, &rp, &ws, &wsr, x, &S, &st, &ne, &tf, 1, rounding); break;
+        case P_UNIFORM_F16: traj_uniform(&md, &rp, &ws, &wsr, x, &S, &st, &ne, &tf, 0, rounding); break;
+        default: traj_uniform(&md, &rp, &ws, &wsr, x, &S, &st, &ne, &tf, 1, rounding); break;
+        }
+        if (status) status[r] = st;
+        if (n_events) n_events[r] = ne;
+        if (t_final) t_final[r] = tf;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Array forms of the scalar primitives, for the pin tests.                   */
+/* ------------------------------------------------------------------------ */
+void oracle_f32_to_f16_array(const float *x, int64_t n, int sr, const uint32_t *r, uint16_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_f32_to_f16(x[i], sr, r ? r[i] : 0u);
+}
+
+void oracle_f32_to_bf16_array(const float *x, int64_t n, int sr, const uint32_t *r, uint16_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_f32_to_bf16(x[i], sr, r ? r[i] : 0u);
+}
+
+void oracle_f16_to_f32_array(const uint16_t *h, int64_t n, float *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_f16_to_f32(h[i]);
+}
+
+void oracle_log_f32_array(const float *x, int64_t n, float *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_log_f32(x[i]);
+}
+
+void oracle_log_f64_array(const double *x, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_log_f64(x[i]);
+}
+
+/* Philox blocks for counters (c0 + i, c1, c2, c3), i = 0..n-1 (no carry). */
+void oracle_philox_array(const uint32_t ctr[4], const uint32_t key[2], int64_t n, uint32_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t c[4];
+        c[0] = ctr[0] + (uint32_t)i; c[1] = ctr[1]; c[2] = ctr[2]; c[3] = ctr[3];
+        oracle_philox4x32_10(c, key, out + 4 * i);
+    }
+}

@@ -58,9 +58,11 @@
  *      u1 = (w0 + 1) 2^-32 in (0,1] and u2 = w1 2^-32 in [0,1) in FP64 mode,
  *      u1 = ((w0 >> 8) + 1) 2^-24 and u2 = (w1 >> 8) 2^-24 otherwise, so every
  *      mode sees the same draws (common random numbers).  Stream 1 holds the
- *      SR bits: with S rounding operations per step, step n owns words
- *      [n*ceil(S/2), (n+1)*ceil(S/2)) and operation i takes the low (even i) or
- *      high (odd i) half of word i/2.  RN modes never read stream 1.
+ *      SR bits: with S rounding operations per step and B = ceil(S/8), step n
+ *      owns the whole blocks [n*B, (n+1)*B), i.e. words [4nB, 4nB + 4B), and
+ *      operation i takes the low (even i) or high (odd i) half of word
+ *      4nB + i/2; the unused tail of the last block is discarded.  RN modes
+ *      never read stream 1.
  *   R7 uniform mode: E = rnd(-log(u1)) with log evaluated in binary32 on u1,
  *      U2 = rnd(u2), tau = rnd(E / a0), target = rnd(U2 * a0),
  *      t_new = rnd(t + tau).  SR operation order within a step: propensity
@@ -568,7 +570,7 @@ static void traj_f32_mixed(const omodel *md, const runp *rp, word_stream *ws, wo
         cp[j] = c; h0[j] = g0; h1[j] = g1;
         if (mixed && sr) nsr += chain_ops(md, j);
     }
-    const uint64_t Ws = (uint64_t)((nsr + 1) / 2);   /* SR words per step */
+    const uint64_t Ws = 4u * (uint64_t)((nsr + 7) / 8);   /* SR words per step: whole blocks */
     float t_end = (float)rp->t_end;
     float smp[1024];
     for (int kk = 0; kk < rp->K; ++kk) smp[kk] = (float)rp->samples[kk];
@@ -626,7 +628,7 @@ static void traj_uniform(const omodel *md, const runp *rp, word_stream *ws, word
         nsr += chain_ops(md, j);
     }
     nsr += (M - 1) + 5;   /* partial sums, E, U2, tau, target, t_new */
-    const uint64_t Ws = (uint64_t)((nsr + 1) / 2);   /* SR words per step */
+    const uint64_t Ws = 4u * (uint64_t)((nsr + 7) / 8);   /* SR words per step: whole blocks */
     float t_end = rn16(fmt, (float)rp->t_end);
     float smp[1024];
     for (int kk = 0; kk < rp->K; ++kk) smp[kk] = rn16(fmt, (float)rp->samples[kk]);

@@ -1,0 +1,387 @@
+"""Benchmark: SSA reaction events/s on one GB300 for the 16-bit precision modes,
+against the same engine's fp64 mode.
+
+Workload (the Schloegl configuration): the bistable Schloegl model (c1 = 3e-7,
+c2 = 1e-4, c3 = 1e-3, c4 = 3.5, reservoirs A = 1e5 and B = 2e5 folded into the
+rate constants), X0 = 250, 10^6 trajectories per GPU, t_end = 10, 50 evenly
+spaced snapshots.  One step runs the five 16-bit modes (mixed fp16 RN, mixed
+bf16 RN, uniform fp16 RN, uniform fp16 SR, uniform bf16 SR) over the whole
+ensemble; fp64 is timed the same way beside it.  Trajectories are
+independent, so N GPUs run N disjoint trajectory-id ranges (weak scaling, no
+collective on the data path).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_00479_gb300 import presets as P  # noqa: E402
+
+METRIC = "SSA reaction events/s on 1 GB300, 16-bit modes vs fp64, at KS p>0.05 vs oracle"
+MODES16 = [("mixed_f16", "rn"), ("mixed_bf16", "rn"), ("uniform_f16", "rn"), ("uniform_f16", "sr"),
+           ("uniform_bf16", "sr")]
+N_TRAJ = 1_000_000
+T_END = 10.0
+K_SAMPLES = 50
+MAX_EVENTS = 200_000
+SEED = 2605
+SEED_FP64 = 2606     # independent fp64 ensemble for the KS / W1 comparison
+
+
+def workload():
+    m = P.schlogl()
+    return m, P.schlogl_x0(m), P.even_samples(T_END, K_SAMPLES)
+
+
+# ----------------------------------------------------------- op accounting
+# Algorithmic 32-bit operations per event for the Schloegl structure with the
+# reservoirs folded (chains: X(X-1) in reaction 1, X(X-1)(X-2) in reaction 2,
+# X in reaction 4; reaction 3 is a constant).  Counted from the method:
+#   Philox4x32-10 block: 10 rounds x (2 mul-hi + 2 mul-lo + 4 xor + 2 add) = 100
+#   uniforms: half a block per step (two steps per block) + 2 x 4 to scale
+#   log: 25 (exponent split 6, s = (m-1)/(m+1) 3, z and series 8, recombine 8)
+#   tau division, target multiply, clock add: 3
+#   mass-action factor: subtract, convert, multiply = 3 (+2 roundings in 16 bit)
+#   partial sums: M - 1 adds (+ M - 1 roundings in uniform mode)
+#   selection M compares + branch 2, update 2, snapshot compare 1, loop 4
+SCHLOGL_FACTORS = 6  # X(X-1): 2, X(X-1)(X-2): 3, X: 1
+M_REACTIONS = 4
+
+
+def ops_per_event(prec, rnd):
+    philox = 100
+    ops = philox * 0.5 + 8 + 25 + 3
+    ops += SCHLOGL_FACTORS * 3
+    ops += (M_REACTIONS - 1)
+    ops += M_REACTIONS + 2 + 2 + 1 + 4
+    if prec.startswith(("mixed", "uniform")):
+        ops += SCHLOGL_FACTORS * 2          # cvt to and from the 16-bit type
+    if prec.startswith("uniform"):
+        ops += (M_REACTIONS - 1 + 5) * 2    # rounded sums, E, U2, tau, target, t
+    if rnd == "sr":
+        n_sr = SCHLOGL_FACTORS * 2 + (M_REACTIONS - 1 + 5 if prec.startswith("uniform") else 0)
+        ops += philox * ((n_sr + 7) // 8)   # stochastic-rounding blocks per step
+    return float(ops)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def start(self):
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                           "--format=csv,noheader,nounits", "-lms", "200"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self._proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------ distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------- the CPU oracle
+def oracle_sample(n_per_mode, modes, workers):
+    """Time the oracle (as it stands) on a bounded sample of the workload."""
+    import oracle
+    m, x0, samples = workload()
+    events = 0
+    t0 = time.perf_counter()
+    for prec, rnd in modes:
+        r = oracle.run_parallel(m, x0, n_per_mode, T_END, samples, workers=workers, precision=prec, rounding=rnd,
+                                normalise=True, seed=SEED, max_events=MAX_EVENTS)
+        events += int(r["n_events"].sum())
+    dt = time.perf_counter() - t0
+    return events, dt
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the oracle on the host cores, same metric and config."""
+    if rank != 0:
+        return
+    workers = os.cpu_count() or 1
+    n_per_mode = 32 * workers
+    for _ in range(args.warmup):
+        oracle_sample(max(workers, 16), MODES16, workers)
+    times, evs = [], []
+    for _ in range(args.steps):
+        e, dt = oracle_sample(n_per_mode, MODES16, workers)
+        times.append(dt)
+        evs.append(e)
+    total_t, total_e = sum(times), sum(evs)
+    value = total_e / total_t
+    sample = f"{n_per_mode} trajectories per 16-bit mode per step (of {N_TRAJ}), trajectory ids 0..{n_per_mode - 1}"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16,bf16",
+        "data": "synthetic", "config": config_block(),
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": workers, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_block():
+    return {"workload": f"schlogl bistable, {N_TRAJ} trajectories per GPU, t_end={T_END}, {K_SAMPLES} snapshots, "
+                        "reservoirs folded (normalise), int32 state",
+            "model": "schlogl", "n_traj_per_gpu": N_TRAJ, "t_end": T_END, "n_samples": K_SAMPLES,
+            "modes": [f"{p}:{r}" for p, r in MODES16], "baseline_mode": "fp64", "max_events": MAX_EVENTS,
+            "l2": "no input reuse; each launch writes 600 MB of snapshots (> 129 MB L2)"}
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import torch
+    from oracle import stats
+    from paper_2605_00479_gb300 import ssa
+
+    torch.cuda.set_device(local)
+    ssa.lib()
+    m_dict, x0, samples = workload()
+    model = ssa.Model.from_dict(m_dict)
+    offset = rank * N_TRAJ
+    dev = torch.device("cuda", local)
+    out = torch.empty((K_SAMPLES, model.N, N_TRAJ), dtype=torch.int32, device=dev)
+    status = torch.empty(N_TRAJ, dtype=torch.int32, device=dev)
+    nev = torch.empty(N_TRAJ, dtype=torch.int64, device=dev)
+    tfin = torch.empty(N_TRAJ, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def launch(prec, rnd, seed):
+        ssa.ensemble_run(model, N_TRAJ, x0, T_END, samples, prec, rnd, True, seed, MAX_EVENTS, 4, out=out,
+                         status=status, n_events=nev, t_final=tfin, stream=stream, traj_offset=offset)
+
+    def one_step(modes, seed, record):
+        per = []
+        for prec, rnd in modes:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launch(prec, rnd, seed)
+            e1.record(stream)
+            per.append((prec, rnd, e0, e1))
+            if record is not None:
+                # event totals and final states, read after the launch (outside the kernel's events)
+                record.setdefault((prec, rnd), []).append((nev.sum(), out[-1, 0].clone(), status.clone()))
+        return per
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        one_step(MODES16, SEED, None)
+    one_step([("fp64", "rn")], SEED_FP64, None)
+    torch.cuda.synchronize()
+
+    # timed: K steps of the five 16-bit modes
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    rec = {}
+    t0 = time.perf_counter()
+    steps = [one_step(MODES16, SEED, rec) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    clocks.stop()
+    kernel_ms = {}
+    for per in steps:
+        for prec, rnd, e0, e1 in per:
+            kernel_ms.setdefault((prec, rnd), []).append(e0.elapsed_time(e1))
+    step_ms = [sum(e0.elapsed_time(e1) for _, _, e0, e1 in per) for per in steps]
+    local_time = sum(step_ms) / 1e3
+    events = {k: float(sum(float(v[0]) for v in vals)) for k, vals in rec.items()}
+    local_events = sum(events.values())
+
+    # fp64 beside it, same number of launches
+    rec64 = {}
+    steps64 = [one_step([("fp64", "rn")], SEED_FP64, rec64) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    fp64_ms = [e0.elapsed_time(e1) for per in steps64 for _, _, e0, e1 in per]
+    fp64_events = sum(float(v[0]) for v in rec64[("fp64", "rn")])
+    fp64_rate = fp64_events / (sum(fp64_ms) / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    h_out = torch.empty((K_SAMPLES, model.N, N_TRAJ), dtype=torch.int32).pin_memory()
+    h_st = torch.empty(N_TRAJ, dtype=torch.int32).pin_memory()
+    h_ev = torch.empty(N_TRAJ, dtype=torch.int64).pin_memory()
+    h_tf = torch.empty(N_TRAJ, dtype=torch.float64).pin_memory()
+    e2e_events, e2e_time = 0.0, 0.0
+    h2d = d2h = 0
+    for prec, rnd in MODES16:
+        t1 = time.perf_counter()
+        ssa.ensemble_run_host(model, N_TRAJ, x0, T_END, samples, prec, rnd, True, SEED, MAX_EVENTS, 4,
+                              out=h_out.numpy(), status=h_st.numpy().view(np.uint32), n_events=h_ev.numpy(),
+                              t_final=h_tf.numpy(), traj_offset=offset)
+        e2e_time += time.perf_counter() - t1
+        e2e_events += float(h_ev.numpy().sum())
+        h2d += x0.nbytes + samples.nbytes
+        d2h += h_out.numel() * 4 + h_st.numel() * 4 + h_ev.numel() * 8 + h_tf.numel() * 8
+
+    # whole-job numbers
+    job_time = max_over_ranks(world, local_time)
+    job_events = sum_over_ranks(world, local_events)
+    e2e_time = max_over_ranks(world, e2e_time)
+    e2e_events = sum_over_ranks(world, e2e_events)
+    fp64_rate_job = sum_over_ranks(world, fp64_rate)
+    if rank != 0:
+        return
+
+    # accuracy of each mode against the independent fp64 ensemble (last step)
+    ref = rec64[("fp64", "rn")][-1][1].cpu().numpy()
+    modes_out = {}
+    for (prec, rnd), vals in rec.items():
+        xs = vals[-1][1].cpu().numpy()
+        st = vals[-1][2].cpu().numpy()
+        D, p = stats.ks_2samp(ref, xs)
+        ms = kernel_ms[(prec, rnd)]
+        rate = events[(prec, rnd)] / (sum(ms) / 1e3)
+        modes_out[f"{prec}:{rnd}"] = {
+            "events_per_s": rate, "ms_per_launch": float(np.mean(ms)), "speedup_vs_fp64": rate / fp64_rate,
+            "ks_p_vs_fp64": p, "w1_vs_fp64": stats.wasserstein1(ref, xs), "mean": float(xs.mean()),
+            "var": float(xs.var()), "frac_max_events": float(np.mean((st & 2) != 0)),
+            "ops_per_event": ops_per_event(prec, rnd)}
+    modes_out["fp64:rn"] = {"events_per_s": fp64_rate, "ms_per_launch": float(np.mean(fp64_ms)),
+                            "mean": float(ref.mean()), "var": float(ref.var())}
+
+    # roofline of the dominant kernel (largest share of the step)
+    dom = max(kernel_ms, key=lambda k: sum(kernel_ms[k]))
+    dom_ms = float(np.mean(kernel_ms[dom]))
+    dom_events = events[dom] / args.steps
+    clk = clocks.summary()
+    sm_mhz = clk["sm_mhz"] or 1455.0
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_gops = sms * 128 * sm_mhz * 1e6 / 1e9            # 4 schedulers x 32 lanes per SM per clock
+    achieved_gops = ops_per_event(*dom) * dom_events / (dom_ms / 1e3) / 1e9
+    value = job_events / job_time
+    line = {
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * job_time / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16,bf16", "data": "synthetic", "config": config_block(),
+        "gpu_launches": len(MODES16) * args.steps,
+        "roofline": {"bound": "alu", "kernel": f"ssa_kernel<schlogl,{dom[0]},{dom[1]}>",
+                     "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
+                     "frac": achieved_gops / peak_gops, "traffic": None,
+                     "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock sampled in the run)",
+                     "snapshot_hbm_gbs": (K_SAMPLES * model.N * N_TRAJ * 4) / (dom_ms / 1e3) / 1e9},
+        "fp64_events_per_s": fp64_rate_job, "speedup_vs_fp64": value / fp64_rate_job,
+        "modes": modes_out,
+        "e2e": {"value": e2e_events / e2e_time, "unit": "events/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        workers = os.cpu_count() or 1
+        n_per_mode = 32 * workers
+        e, dt = oracle_sample(n_per_mode, MODES16, workers)
+        line["cpu_baseline"] = {"value": e / dt, "unit": "events/s", "cores": workers, "kind": "oracle",
+                                "sample": f"{n_per_mode} trajectories per 16-bit mode (ids 0..{n_per_mode - 1}) "
+                                          f"of the same workload, one process per core"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

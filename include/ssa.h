@@ -1,0 +1,177 @@
+/*
+ * ssa.h -- C ABI of the GB300 ensemble engine for the reduced-precision
+ * Gillespie direct method (Kimpson, Flegg & Flegg, "Reduced-Precision
+ * Stochastic Simulation for Mathematical Biology").
+ *
+ * Problem statement (Sec. 2 of the paper): N species X_1..X_N, M reaction
+ * channels R_1..R_M, each with a propensity a_j(x) and a change vector nu_j.
+ * The direct method repeats: compute every a_j and a0 = sum_j a_j; draw
+ * tau = -ln(u1)/a0; fire the smallest mu with sum_{j<=mu} a_j > u2*a0;
+ * x += nu_mu, t += tau.
+ *
+ * Conventions for every entry point:
+ *  - Plain pointers and sizes only.  "host" pointers are read during the call
+ *    and may be freed when it returns; "device" pointers are CUDA global
+ *    memory owned by the caller and must stay valid until the work queued on
+ *    the stream has finished.
+ *  - Functions return SSA_OK (0) or a negative ssa_status.  Invalid arguments
+ *    are rejected on the host before anything is launched (SSA_EINVAL); the
+ *    message is available from ssa_last_error() on the calling thread.
+ *  - Launches are asynchronous on the given CUDA stream (NULL = legacy default
+ *    stream) unless the entry point says otherwise.
+ *  - Per-trajectory problems (overflow, event cap, ...) never abort a launch:
+ *    they are reported as status bits in traj_status[].
+ *  - Results of a trajectory depend only on (model, x0, rates, t_end, sample
+ *    times, precision, rounding, normalise, seed, max_events, global
+ *    trajectory id); never on the launch configuration or on other
+ *    trajectories.
+ */
+#ifndef SSA_H
+#define SSA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssa_model ssa_model;   /* opaque, owned by the library */
+
+/* Propensity laws.
+ * SSA_LAW_MASS_ACTION: a_j = c'_j * prod_i prod_{m<r_ij} (x_i - m), with
+ *   c'_j = c_j / prod_i r_ij!  (Gillespie's c-convention: c_j times the number
+ *   of distinct reactant combinations; Sec. 4.2 Schloegl k2 n(n-1)(n-2),
+ *   Sec. 4.4 dimer kf nA(nA-1)/2).  a_j = 0 when any x_i < r_ij.
+ * SSA_LAW_HILL_REPRESSION: a_j = alpha0 + alpha / (1 + P^h) with P the count
+ *   of the regulator species (Sec. 4.5, repressilator transcription); the
+ *   rate c_j is not used. */
+typedef enum { SSA_LAW_MASS_ACTION = 0, SSA_LAW_HILL_REPRESSION = 1 } ssa_law;
+
+/* Precision modes (Sec. 3.2 and Sec. 4 mode list).  Tp = propensity type,
+ * Ta = type of the propensity sum, Tt = time type; state is int32 in all.
+ *   SSA_FP64          Tp = Ta = Tt = binary64
+ *   SSA_FP32          Tp = Ta = Tt = binary32
+ *   SSA_MIXED_F16     Tp = binary16, Ta = Tt = binary32
+ *   SSA_MIXED_BF16    Tp = bfloat16, Ta = Tt = binary32
+ *   SSA_UNIFORM_F16   every operation rounded to binary16
+ *   SSA_UNIFORM_BF16  every operation rounded to bfloat16 */
+typedef enum {
+    SSA_FP64 = 0, SSA_FP32 = 1, SSA_MIXED_F16 = 2, SSA_MIXED_BF16 = 3,
+    SSA_UNIFORM_F16 = 4, SSA_UNIFORM_BF16 = 5
+} ssa_precision;
+
+/* Rounding of 16-bit operations (Sec. 3.3): round-to-nearest-even, or
+ * stochastic rounding applied after every operation whose result has the
+ * 16-bit type.  SR is valid only with the four 16-bit modes. */
+typedef enum { SSA_RN = 0, SSA_SR = 1 } ssa_rounding;
+
+typedef enum {
+    SSA_OK = 0, SSA_EINVAL = -1, SSA_ENOMEM = -2, SSA_ECUDA = -3, SSA_ETIMEDOUT = -4
+} ssa_status;
+
+/* Per-trajectory status bits written to traj_status[]. */
+enum {
+    SSA_TRAJ_OVERFLOW = 1,     /* a0 = +inf: the trajectory stops at its current state */
+    SSA_TRAJ_MAX_EVENTS = 2,   /* the event cap was reached before t_end */
+    SSA_TRAJ_STATE_RANGE = 4,  /* a count went negative, or did not fit int16 storage */
+    SSA_TRAJ_NAN = 8           /* a0 = NaN */
+};
+
+/* Limits of this build. */
+enum { SSA_MAX_SPECIES = 8, SSA_MAX_REACTIONS = 16, SSA_MAX_ORDER = 3, SSA_MAX_HILL = 4,
+       SSA_MAX_SAMPLES = 1024 };
+
+/*
+ * ssa_model_create -- describe a reaction network (Sec. 2 problem statement).
+ *   n_species         N, 1..SSA_MAX_SPECIES
+ *   n_reactions       M, 1..SSA_MAX_REACTIONS
+ *   reactant_order    host [M][N] row-major, r_ij in 0..SSA_MAX_ORDER
+ *   stoich            host [M][N] row-major, net change nu_ij
+ *   rate              host [M] c-convention constants c_j >= 0 (finite)
+ *   law               host [M] ssa_law, or NULL for all mass action
+ *   hill              host [M][4] {alpha0, alpha, h, regulator} for Hill rows
+ *                     (h integer 1..SSA_MAX_HILL, regulator a species index),
+ *                     or NULL when no row uses SSA_LAW_HILL_REPRESSION
+ *   constant_species  host [N], 1 = reservoir held at its initial count
+ *                     (its nu entries are ignored), or NULL for none
+ *   out               receives the model handle
+ * Errors: SSA_EINVAL on any out-of-range entry; SSA_ENOMEM.
+ */
+int ssa_model_create(int n_species, int n_reactions, const int32_t *reactant_order,
+                     const int32_t *stoich, const double *rate, const int32_t *law,
+                     const double *hill, const uint8_t *constant_species, ssa_model **out);
+
+/* Release a model (NULL is allowed).  No launch may still be using it. */
+void ssa_model_destroy(ssa_model *model);
+
+/* Which compiled kernel family serves this model: 0 = general table-driven
+ * kernel, >0 = a structure-specialised kernel (1 birth-death, 2 Schloegl,
+ * 3 telegraph, 4 dimer, 5 repressilator).  Negative on a NULL model. */
+int ssa_model_kernel_family(const ssa_model *model);
+
+/*
+ * ssa_ensemble_run -- simulate n_traj independent trajectories of one model
+ * from one initial state, one trajectory per GPU lane.
+ *   n_traj        number of trajectories, >= 0
+ *   traj_offset   global id of the first trajectory; ids offset..offset+n_traj-1
+ *                 must fit in 32 bits.  Trajectory r draws its random numbers
+ *                 from Philox4x32-10 streams keyed by (seed, offset + r).
+ *   x0            host [N] initial counts (>= 0)
+ *   t_end         final time, finite, > 0
+ *   n_samples     K, 1..SSA_MAX_SAMPLES
+ *   sample_times  host [K] ascending, 0 <= s_k <= t_end.  Snapshot k holds
+ *                 the state after every event at time <= s_k.
+ *   precision, rounding   see above
+ *   normalise     1: fold constant species into the rate constants in
+ *                 binary64 before rounding to Tp (Sec. 4.2 rescaling)
+ *   seed          64-bit Philox key
+ *   max_events    event cap per trajectory, >= 0
+ *   state_bytes   4 (int32 snapshots) or 2 (int16; values are clamped and
+ *                 flagged SSA_TRAJ_STATE_RANGE when out of range)
+ *   out           device [K][N][n_traj], trajectory index fastest
+ *   traj_status   device [n_traj] status bits
+ *   n_events      device [n_traj] events fired per trajectory, or NULL
+ *   t_final       device [n_traj] time of the last event (widened), or NULL
+ *   stream        cudaStream_t, or NULL
+ * The call allocates an 8-byte work-queue counter with stream-ordered
+ * allocation and frees it after the launch.
+ * Errors: SSA_EINVAL (arguments), SSA_ENOMEM, SSA_ECUDA (launch failure).
+ */
+int ssa_ensemble_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset,
+                     const int32_t *x0, double t_end, int n_samples, const double *sample_times,
+                     int precision, int rounding, int normalise, uint64_t seed,
+                     int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
+                     int64_t *n_events, double *t_final, void *stream);
+
+/*
+ * ssa_ensemble_run_host -- ssa_ensemble_run with HOST output buffers.  The
+ * call allocates device buffers, launches, copies the results back and
+ * synchronises the stream before returning.  out, traj_status, n_events and
+ * t_final are host pointers with the layouts above (n_events, t_final may be
+ * NULL).  Page-locked host memory makes the copies faster.
+ */
+int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_offset,
+                          const int32_t *x0, double t_end, int n_samples, const double *sample_times,
+                          int precision, int rounding, int normalise, uint64_t seed,
+                          int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
+                          int64_t *n_events, double *t_final, void *stream);
+
+/*
+ * ssa_set_launch_config -- launch shape for subsequent runs in this process.
+ *   threads_per_block  multiple of 32 in 32..256
+ *   blocks_per_sm      resident blocks per SM to launch (0 = as many as the
+ *                      occupancy calculator allows)
+ * Results never depend on the launch shape; only speed does.  Not
+ * synchronised with concurrent launches from other threads.
+ * Errors: SSA_EINVAL.
+ */
+int ssa_set_launch_config(int threads_per_block, int blocks_per_sm);
+
+/* Thread-local description of the last error on the calling thread. */
+const char *ssa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSA_H */

@@ -1,0 +1,358 @@
+// ssa_capi.cu -- host side of the C ABI declared in include/ssa.h.
+//
+// Validates arguments, matches the model against the compiled structure
+// families, prepares the rate constants (Gillespie c-convention, binary64)
+// and launches the persistent kernel.  Everything that touches trajectory
+// data runs in the CUDA kernels; this file only marshals.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/ssa.h"
+#include "ssa_launch.h"
+#include "ssa_models.h"
+
+struct ssa_model {
+    int N, M;
+    int32_t order[ssa::kMaxM][ssa::kMaxN];
+    int32_t stoich[ssa::kMaxM][ssa::kMaxN];
+    double rate[ssa::kMaxM];
+    int32_t law[ssa::kMaxM];
+    double hill[ssa::kMaxM][4];
+    uint8_t constant[ssa::kMaxN];
+    int family;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(SSA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+ssa::LaunchConfig g_cfg = {128, 0};
+
+template <class S>
+bool matches(const ssa_model &m)
+{
+    if (m.N != S::N || m.M != S::M) return false;
+    for (int i = 0; i < S::N; ++i)
+        if ((m.constant[i] != 0) != (S::cs[i] != 0)) return false;
+    for (int j = 0; j < S::M; ++j) {
+        if (m.law[j] != S::lw[j]) return false;
+        if (S::lw[j] == SSA_LAW_HILL_REPRESSION) {
+            if ((int)m.hill[j][2] != S::hh[j] || (int)m.hill[j][3] != S::hreg[j]) return false;
+            continue;
+        }
+        for (int i = 0; i < S::N; ++i) {
+            if (m.order[j][i] != S::ord[j][i]) return false;
+            if (!S::cs[i] && m.stoich[j][i] != S::nu[j][i]) return false;
+        }
+    }
+    return true;
+}
+
+int detect_family(const ssa_model &m)
+{
+    if (matches<ssa::models::BirthDeath>(m)) return ssa::models::BirthDeath::family;
+    if (matches<ssa::models::Schlogl>(m)) return ssa::models::Schlogl::family;
+    if (matches<ssa::models::Telegraph>(m)) return ssa::models::Telegraph::family;
+    if (matches<ssa::models::Dimer>(m)) return ssa::models::Dimer::family;
+    if (matches<ssa::models::Repressilator>(m)) return ssa::models::Repressilator::family;
+    return 0;
+}
+
+ssa::Launcher launcher_for(int family)
+{
+    switch (family) {
+    case 1: return ssa::launch_birth_death;
+    case 2: return ssa::launch_schlogl;
+    case 3: return ssa::launch_telegraph;
+    case 4: return ssa::launch_dimer;
+    case 5: return ssa::launch_repressilator;
+    default: return ssa::launch_general;
+    }
+}
+
+bool finite_double(double v) { return std::isfinite(v); }
+
+// c'_j = c_j / prod_i r_ij!, then (normalise) times the falling factorials of
+// the constant species' counts, species ascending, factor m ascending; all in
+// binary64 (reading of Sec. 4.2: k1 A and k3 B formed before rounding).
+void rate_constants(const ssa_model &m, const int32_t *x0, int normalise, double *cprime, int8_t folded[][ssa::kMaxN])
+{
+    for (int j = 0; j < m.M; ++j) {
+        for (int i = 0; i < ssa::kMaxN; ++i) folded[j][i] = 0;
+        if (m.law[j] == SSA_LAW_HILL_REPRESSION) {
+            cprime[j] = 0.0;
+            continue;
+        }
+        double denom = 1.0;
+        for (int i = 0; i < m.N; ++i) {
+            double f = 1.0;
+            for (int q = 2; q <= m.order[j][i]; ++q) f = f * (double)q;
+            denom = denom * f;
+        }
+        double c = m.rate[j] / denom;
+        if (normalise) {
+            for (int i = 0; i < m.N; ++i) {
+                if (!m.constant[i] || m.order[j][i] == 0) continue;
+                for (int q = 0; q < m.order[j][i]; ++q) c = c * (double)(x0[i] - q);
+                folded[j][i] = 1;
+            }
+        }
+        cprime[j] = c;
+    }
+}
+
+int chain_ops(const ssa_model &m, int j, int8_t folded[][ssa::kMaxN])
+{
+    if (m.law[j] == SSA_LAW_HILL_REPRESSION) return (int)m.hill[j][2] + 3;
+    int ops = 0;
+    for (int i = 0; i < m.N; ++i)
+        if (!folded[j][i]) ops += 2 * m.order[j][i];
+    return ops;
+}
+
+int validate_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, const int32_t *x0, double t_end,
+                 int n_samples, const double *sample_times, int precision, int rounding, int64_t max_events,
+                 int state_bytes)
+{
+    if (!model) return fail(SSA_EINVAL, "model is NULL");
+    if (n_traj < 0) return fail(SSA_EINVAL, "n_traj must be >= 0");
+    if (traj_offset + (uint64_t)n_traj > 0x100000000ull) return fail(SSA_EINVAL, "trajectory ids must fit in 32 bits");
+    if (!x0) return fail(SSA_EINVAL, "x0 is NULL");
+    for (int i = 0; i < model->N; ++i)
+        if (x0[i] < 0) return fail(SSA_EINVAL, "x0[%d] is negative", i);
+    if (!finite_double(t_end) || !(t_end > 0.0)) return fail(SSA_EINVAL, "t_end must be finite and > 0");
+    if (n_samples < 1 || n_samples > SSA_MAX_SAMPLES) return fail(SSA_EINVAL, "n_samples must be in 1..%d", SSA_MAX_SAMPLES);
+    if (!sample_times) return fail(SSA_EINVAL, "sample_times is NULL");
+    for (int k = 0; k < n_samples; ++k) {
+        const double s = sample_times[k];
+        if (!finite_double(s) || s < 0.0 || s > t_end) return fail(SSA_EINVAL, "sample_times[%d] outside [0, t_end]", k);
+        if (k > 0 && s < sample_times[k - 1]) return fail(SSA_EINVAL, "sample_times must be ascending");
+    }
+    if (precision < SSA_FP64 || precision > SSA_UNIFORM_BF16) return fail(SSA_EINVAL, "unknown precision %d", precision);
+    if (rounding != SSA_RN && rounding != SSA_SR) return fail(SSA_EINVAL, "unknown rounding %d", rounding);
+    if (rounding == SSA_SR && precision < SSA_MIXED_F16) return fail(SSA_EINVAL, "stochastic rounding needs a 16-bit mode");
+    if (max_events < 0) return fail(SSA_EINVAL, "max_events must be >= 0");
+    if (state_bytes != 2 && state_bytes != 4) return fail(SSA_EINVAL, "state_bytes must be 2 or 4");
+    return SSA_OK;
+}
+
+// Fill the kernel arguments common to single and batched runs.
+void fill_structure(const ssa_model &m, int normalise, const int32_t *x0, ssa::RunArgs &a)
+{
+    a.N = m.N;
+    a.M = m.M;
+    rate_constants(m, x0, normalise, a.cprime, a.folded);
+    int start = 0;
+    for (int j = 0; j < m.M; ++j) {
+        a.chain_start[j] = (int16_t)start;
+        start += chain_ops(m, j, a.folded);
+        a.law[j] = (int8_t)m.law[j];
+        a.hill_h[j] = (int8_t)(m.law[j] == SSA_LAW_HILL_REPRESSION ? (int)m.hill[j][2] : 0);
+        a.hill_reg[j] = (int8_t)(m.law[j] == SSA_LAW_HILL_REPRESSION ? (int)m.hill[j][3] : 0);
+        a.hill_a0[j] = m.law[j] == SSA_LAW_HILL_REPRESSION ? m.hill[j][0] : 0.0;
+        a.hill_a[j] = m.law[j] == SSA_LAW_HILL_REPRESSION ? m.hill[j][1] : 0.0;
+        for (int i = 0; i < m.N; ++i) {
+            a.order[j][i] = (int8_t)m.order[j][i];
+            a.stoich[j][i] = m.constant[i] ? 0 : m.stoich[j][i];
+        }
+    }
+    a.sr_ops = start;   // rounding operations in the propensity chains of one step
+    for (int i = 0; i < m.N; ++i) a.x0[i] = x0[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ssa_last_error(void) { return g_last_error.c_str(); }
+
+int ssa_set_launch_config(int threads_per_block, int blocks_per_sm)
+{
+    if (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32 != 0)
+        return fail(SSA_EINVAL, "threads_per_block must be a multiple of 32 in 32..256");
+    if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(SSA_EINVAL, "blocks_per_sm must be in 0..64");
+    g_cfg.block = threads_per_block;
+    g_cfg.blocks_per_sm = blocks_per_sm;
+    return SSA_OK;
+}
+
+int ssa_model_create(int n_species, int n_reactions, const int32_t *reactant_order, const int32_t *stoich,
+                     const double *rate, const int32_t *law, const double *hill, const uint8_t *constant_species,
+                     ssa_model **out)
+{
+    if (!out) return fail(SSA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_species < 1 || n_species > SSA_MAX_SPECIES) return fail(SSA_EINVAL, "n_species must be in 1..%d", SSA_MAX_SPECIES);
+    if (n_reactions < 1 || n_reactions > SSA_MAX_REACTIONS)
+        return fail(SSA_EINVAL, "n_reactions must be in 1..%d", SSA_MAX_REACTIONS);
+    if (!reactant_order || !stoich || !rate) return fail(SSA_EINVAL, "reactant_order, stoich and rate are required");
+    ssa_model *m = new (std::nothrow) ssa_model;
+    if (!m) return fail(SSA_ENOMEM, "out of host memory");
+    std::memset(m, 0, sizeof(*m));
+    m->N = n_species;
+    m->M = n_reactions;
+    for (int i = 0; i < n_species; ++i) m->constant[i] = constant_species ? (constant_species[i] ? 1 : 0) : 0;
+    for (int j = 0; j < n_reactions; ++j) {
+        m->law[j] = law ? law[j] : SSA_LAW_MASS_ACTION;
+        if (m->law[j] != SSA_LAW_MASS_ACTION && m->law[j] != SSA_LAW_HILL_REPRESSION) {
+            delete m;
+            return fail(SSA_EINVAL, "law[%d] unknown", j);
+        }
+        m->rate[j] = rate[j];
+        if (m->law[j] == SSA_LAW_MASS_ACTION && (!finite_double(rate[j]) || rate[j] < 0.0)) {
+            delete m;
+            return fail(SSA_EINVAL, "rate[%d] must be finite and >= 0", j);
+        }
+        for (int i = 0; i < n_species; ++i) {
+            const int r = reactant_order[j * n_species + i];
+            if (r < 0 || r > SSA_MAX_ORDER) {
+                delete m;
+                return fail(SSA_EINVAL, "reactant_order[%d][%d] must be in 0..%d", j, i, SSA_MAX_ORDER);
+            }
+            m->order[j][i] = r;
+            m->stoich[j][i] = stoich[j * n_species + i];
+        }
+        if (m->law[j] == SSA_LAW_HILL_REPRESSION) {
+            if (!hill) {
+                delete m;
+                return fail(SSA_EINVAL, "hill table required for Hill reactions");
+            }
+            for (int q = 0; q < 4; ++q) m->hill[j][q] = hill[j * 4 + q];
+            const double h = m->hill[j][2], reg = m->hill[j][3];
+            if (!finite_double(m->hill[j][0]) || !finite_double(m->hill[j][1]) || m->hill[j][0] < 0 || m->hill[j][1] < 0 ||
+                h != std::floor(h) || h < 1 || h > SSA_MAX_HILL || reg != std::floor(reg) || reg < 0 || reg >= n_species) {
+                delete m;
+                return fail(SSA_EINVAL, "hill[%d] must be {alpha0>=0, alpha>=0, h in 1..%d, regulator species}", j, SSA_MAX_HILL);
+            }
+            for (int i = 0; i < n_species; ++i) m->order[j][i] = 0;
+        }
+    }
+    m->family = detect_family(*m);
+    *out = m;
+    return SSA_OK;
+}
+
+void ssa_model_destroy(ssa_model *model) { delete model; }
+
+int ssa_model_kernel_family(const ssa_model *model) { return model ? model->family : -1; }
+
+int ssa_ensemble_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, const int32_t *x0, double t_end,
+                     int n_samples, const double *sample_times, int precision, int rounding, int normalise,
+                     uint64_t seed, int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
+                     int64_t *n_events, double *t_final, void *stream)
+{
+    int rc = validate_run(model, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
+                          max_events, state_bytes);
+    if (rc != SSA_OK) return rc;
+    if (n_traj > 0 && (!out || !traj_status)) return fail(SSA_EINVAL, "out and traj_status are required");
+    if (n_traj == 0) return SSA_OK;
+
+    ssa::RunArgs *a = new (std::nothrow) ssa::RunArgs;
+    if (!a) return fail(SSA_ENOMEM, "out of host memory");
+    std::memset(a, 0, sizeof(*a));
+    fill_structure(*model, normalise, x0, *a);
+    a->K = n_samples;
+    a->n_traj = n_traj;
+    a->traj_offset = (uint32_t)traj_offset;
+    a->n_sets = 1;
+    a->traj_per_set = n_traj;
+    a->t_end = t_end;
+    for (int k = 0; k < n_samples; ++k) a->samples[k] = sample_times[k];
+    a->key0 = (uint32_t)seed;
+    a->key1 = (uint32_t)(seed >> 32);
+    a->max_events = max_events;
+    a->out = out;
+    a->state_bytes = state_bytes;
+    a->status = traj_status;
+    a->n_events = n_events;
+    a->t_final = t_final;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long *head = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&head), sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        delete a;
+        return e == cudaErrorMemoryAllocation ? fail(SSA_ENOMEM, "work-queue counter: out of device memory")
+                                              : cuda_fail(e, "cudaMallocAsync");
+    }
+    e = cudaMemsetAsync(head, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(head, s);
+        delete a;
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    a->queue_head = head;
+    const bool norm = normalise != 0;
+    int grid = 0;
+    e = launcher_for(model->family)(*a, precision, rounding, norm ? 1 : 0, g_cfg, s, &grid);
+    cudaError_t e2 = cudaFreeAsync(head, s);
+    delete a;
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return SSA_OK;
+}
+
+int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, const int32_t *x0,
+                          double t_end, int n_samples, const double *sample_times, int precision, int rounding,
+                          int normalise, uint64_t seed, int64_t max_events, int state_bytes, void *out,
+                          uint32_t *traj_status, int64_t *n_events, double *t_final, void *stream)
+{
+    int rc = validate_run(model, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
+                          max_events, state_bytes);
+    if (rc != SSA_OK) return rc;
+    if (n_traj > 0 && (!out || !traj_status)) return fail(SSA_EINVAL, "out and traj_status are required");
+    if (n_traj == 0) return SSA_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t out_bytes = (size_t)n_samples * (size_t)model->N * (size_t)n_traj * (size_t)state_bytes;
+    const size_t st_bytes = (size_t)n_traj * sizeof(uint32_t);
+    const size_t ev_bytes = n_events ? (size_t)n_traj * sizeof(int64_t) : 0;
+    const size_t tf_bytes = t_final ? (size_t)n_traj * sizeof(double) : 0;
+    char *d = nullptr;
+    const size_t total = out_bytes + st_bytes + ev_bytes + tf_bytes + 64;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d), total, s);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(SSA_ENOMEM, "device buffers") : cuda_fail(e, "cudaMallocAsync");
+    // 8-byte aligned sub-buffers: int64/double arrays first
+    char *p = d;
+    int64_t *d_ev = ev_bytes ? reinterpret_cast<int64_t *>(p) : nullptr; p += ev_bytes;
+    double *d_tf = tf_bytes ? reinterpret_cast<double *>(p) : nullptr; p += tf_bytes;
+    uint32_t *d_st = reinterpret_cast<uint32_t *>(p); p += st_bytes;
+    void *d_out = p;
+    rc = ssa_ensemble_run(model, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
+                          normalise, seed, max_events, state_bytes, d_out, d_st, d_ev, d_tf, stream);
+    if (rc == SSA_OK) {
+        e = cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(traj_status, d_st, st_bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && ev_bytes) e = cudaMemcpyAsync(n_events, d_ev, ev_bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && tf_bytes) e = cudaMemcpyAsync(t_final, d_tf, tf_bytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync");
+    }
+    cudaFreeAsync(d, s);
+    e = cudaStreamSynchronize(s);
+    if (rc == SSA_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,795 @@
+// ssa_device.cuh -- device side of the GB300 ensemble engine for the
+// reduced-precision Gillespie direct method.
+//
+// One GPU lane runs one trajectory at a time; a lane whose trajectory has
+// finished takes the next one from a device work queue (warp-aggregated
+// atomicAdd), so warps stay full while trajectories of very different
+// lengths retire.  State, propensities and partial sums live in registers;
+// the model structure is either compiled in (structure-specialised kernels)
+// or read from kernel parameters (the general kernel).
+//
+// Arithmetic contract (the paper's Sec. 2 direct method, Sec. 3.2 precision
+// partition, Sec. 3.3 stochastic rounding; readings where it is silent):
+//  * c'_j is rounded to the propensity type once, by RN (binary64 ->
+//    binary32 -> 16-bit).
+//  * Mass action: a = c'; for species i ascending, m = 0..r-1:
+//    f = rnd(x_i - m); a = rnd(a * f).  a = +0 when some x_i < r_ij.
+//    Hill: P = rnd(x_reg); q = P; (h-1) times q = rnd(q * P);
+//    d = rnd(1 + q); f = rnd(alpha / d); a = rnd(alpha0 + f).
+//  * A 16-bit operation is the binary32 operation on the widened operands
+//    followed by one rounding (RN: cvt.rn; SR: cvt.rs with 16 random bits of
+//    which binary16 uses the low 13, bfloat16 all 16).
+//  * Random numbers: Philox4x32-10, key = seed, counter = (block lo,
+//    block hi, trajectory id, stream).  Stream 0: step n uses words 2n and
+//    2n+1 (u1 in (0,1], u2 in [0,1)).  Stream 1 (SR bits): step n owns blocks
+//    [n*B, (n+1)*B), B = ceil(S/8) for S rounding operations per step; SR
+//    operation i uses the low (even i) / high (odd i) half of word i/2.
+//  * Uniform mode rounds, in this order: propensity chains, partial sums
+//    S_1..S_{M-1}, E = rnd(-log u1), U2 = rnd(u2), tau = rnd(E / a0),
+//    target = rnd(U2 * a0), t_new = rnd(t + tau).
+//  * log: ln x = e ln2 + 2 atanh(s), s = (m-1)/(m+1), m in [sqrt(1/2),
+//    sqrt(2)], odd series to s^9 (binary32) / s^23 (binary64), ln2 split into
+//    a 16-bit (binary32) or 32-bit (binary64) head and a tail.
+// This file is compiled with -fmad=false: no multiply-add is contracted, so
+// each operation is one IEEE-754 operation in round-to-nearest-even.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+#include <utility>
+
+namespace ssa {
+
+constexpr int kMaxN = 8;
+constexpr int kMaxM = 16;
+constexpr int kMaxK = 1024;
+
+enum Precision { FP64 = 0, FP32 = 1, MIXED_F16 = 2, MIXED_BF16 = 3, UNIFORM_F16 = 4, UNIFORM_BF16 = 5 };
+enum TrajStatus { ST_OVERFLOW = 1, ST_MAX_EVENTS = 2, ST_STATE_RANGE = 4, ST_NAN = 8 };
+
+// Kernel arguments.  Passed by value as a __grid_constant__ parameter (about
+// 10 KB): the model structure for the general kernel, the rate constants of
+// the first parameter set and the sample times ride in parameter space.
+struct RunArgs {
+    // structure (read only by the general kernel)
+    int N, M, K;
+    int sr_ops;                        // rounding operations per step (SR modes)
+    int8_t order[kMaxM][kMaxN];
+    int32_t stoich[kMaxM][kMaxN];      // constant species already zeroed
+    int8_t folded[kMaxM][kMaxN];       // factor folded into c' (normalise)
+    int8_t law[kMaxM];
+    int8_t hill_h[kMaxM];
+    int8_t hill_reg[kMaxM];
+    int16_t chain_start[kMaxM];        // first SR operation of each chain
+    // work
+    int64_t n_traj;                    // work items
+    uint32_t traj_offset;              // global id of item 0
+    int n_sets;                        // parameter sets
+    int64_t traj_per_set;              // item r uses set r / traj_per_set
+    double cprime[kMaxM];              // set 0: c'_j in binary64 (after folding)
+    double hill_a0[kMaxM];
+    double hill_a[kMaxM];
+    int32_t x0[kMaxN];
+    const double *cprime_tab;          // [n_sets][M] when n_sets > 1
+    const double *hill_tab;            // [n_sets][M][2] (alpha0, alpha) or null
+    const int32_t *x0_tab;             // [n_sets][N] or null (then x0 above)
+    double t_end;
+    double samples[kMaxK];
+    uint32_t key0, key1;
+    int64_t max_events;
+    // outputs
+    void *out;                         // [K][N][n_traj] int32 or int16
+    int state_bytes;
+    uint32_t *status;
+    int64_t *n_events;
+    double *t_final;
+    unsigned long long *queue_head;    // zero before launch
+};
+
+// ------------------------------------------------------------------ Philox
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// --------------------------------------------------------------------- log
+__device__ __forceinline__ float log_f32(float x)
+{
+    const float kLn2Hi = 0x1.62e400p-1f;       // leading 16 bits of ln 2
+    const float kLn2Lo = 0x1.7f7d1cp-20f;      // ln 2 - kLn2Hi, rounded
+    uint32_t u = __float_as_uint(x);
+    int e = (int)(u >> 23) - 127;
+    uint32_t mb = (u & 0x7FFFFFu) | 0x3F800000u;
+    if (mb > 0x3FB504F3u) {                     // mantissa above sqrt(2)
+        mb -= 0x00800000u;
+        e += 1;
+    }
+    const float m = __uint_as_float(mb);
+    const float f = m - 1.0f;
+    const float d = m + 1.0f;
+    const float s = f / d;
+    const float z = s * s;
+    float p = 2.0f / 9.0f;
+    p = z * p; p = (2.0f / 7.0f) + p;
+    p = z * p; p = (2.0f / 5.0f) + p;
+    p = z * p; p = (2.0f / 3.0f) + p;
+    float r = s * z;
+    r = r * p;
+    const float two_s = s + s;
+    r = two_s + r;
+    const float ef = (float)e;
+    float lo = ef * kLn2Lo;
+    lo = lo + r;
+    const float hi = ef * kLn2Hi;
+    return hi + lo;
+}
+
+__device__ __forceinline__ double log_f64(double x)
+{
+    const double kLn2Hi = 0x1.62e42fee00000p-1;   // leading 32 bits of ln 2
+    const double kLn2Lo = 0x1.a39ef35793c76p-33;
+    uint64_t u = (uint64_t)__double_as_longlong(x);
+    int e = (int)(u >> 52) - 1023;
+    uint64_t mb = (u & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    if (mb > 0x3FF6A09E667F3BCCull) {
+        mb -= 0x0010000000000000ull;
+        e += 1;
+    }
+    const double m = __longlong_as_double((long long)mb);
+    const double f = m - 1.0;
+    const double d = m + 1.0;
+    const double s = f / d;
+    const double z = s * s;
+    double p = 2.0 / 23.0;
+    p = z * p; p = (2.0 / 21.0) + p;
+    p = z * p; p = (2.0 / 19.0) + p;
+    p = z * p; p = (2.0 / 17.0) + p;
+    p = z * p; p = (2.0 / 15.0) + p;
+    p = z * p; p = (2.0 / 13.0) + p;
+    p = z * p; p = (2.0 / 11.0) + p;
+    p = z * p; p = (2.0 / 9.0) + p;
+    p = z * p; p = (2.0 / 7.0) + p;
+    p = z * p; p = (2.0 / 5.0) + p;
+    p = z * p; p = (2.0 / 3.0) + p;
+    double r = s * z;
+    r = r * p;
+    const double two_s = s + s;
+    r = two_s + r;
+    const double ef = (double)e;
+    double lo = ef * kLn2Lo;
+    lo = lo + r;
+    const double hi = ef * kLn2Hi;
+    return hi + lo;
+}
+
+// --------------------------------------------------------- 16-bit rounding
+// FMT 0: binary16, FMT 1: bfloat16.  Values are carried widened in binary32
+// registers; widening is exact.
+template <int FMT>
+__device__ __forceinline__ float widen16(uint16_t h)
+{
+    if constexpr (FMT == 0) {
+        float y;
+        asm("cvt.f32.f16 %0, %1;" : "=f"(y) : "h"(h));
+        return y;
+    } else {
+        return __uint_as_float((uint32_t)h << 16);
+    }
+}
+
+template <int FMT>
+__device__ __forceinline__ float rn16(float x)
+{
+    uint16_t h;
+    if constexpr (FMT == 0) {
+        asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(x));
+    } else {
+        asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(x));
+    }
+    return widen16<FMT>(h);
+}
+
+// Stochastic rounding with the hardware's paired conversion: the low half of
+// the result rounds operand b with rbits[15:0], the high half operand a with
+// rbits[31:16].  Both operands are x; `hi` picks the half.
+template <int FMT>
+__device__ __forceinline__ float sr16(float x, uint32_t rbits, bool hi)
+{
+    uint32_t d;
+    if constexpr (FMT == 0) {
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(x), "f"(x), "r"(rbits));
+    } else {
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(x), "f"(x), "r"(rbits));
+    }
+    return widen16<FMT>((uint16_t)(hi ? (d >> 16) : (d & 0xFFFFu)));
+}
+
+// ------------------------------------------------------------ mode traits
+template <int PREC>
+struct ModeTraits {
+    static constexpr bool kF64 = PREC == FP64;
+    static constexpr bool kF32 = PREC == FP32;
+    static constexpr bool kMixed = PREC == MIXED_F16 || PREC == MIXED_BF16;
+    static constexpr bool kUniform = PREC == UNIFORM_F16 || PREC == UNIFORM_BF16;
+    static constexpr bool k16 = kMixed || kUniform;
+    static constexpr int kFmt = (PREC == MIXED_BF16 || PREC == UNIFORM_BF16) ? 1 : 0;
+    using P = typename std::conditional<kF64, double, float>::type;   // propensity / sum / time
+};
+
+// Lazily generated SR-stream blocks of the current step.  With operation
+// indices known at compile time the block checks fold away.
+struct SRBits {
+    uint64_t base;     // first block of this step: n * B
+    uint32_t traj, k0, k1;
+    int cur;
+    uint4 blk;
+    __device__ __forceinline__ uint32_t word(int op)
+    {
+        const int b = op >> 3;
+        if (b != cur) {
+            const uint64_t g = base + (uint64_t)b;
+            blk = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), traj, 1u), k0, k1);
+            cur = b;
+        }
+        const int w = (op >> 1) & 3;
+        return w == 0 ? blk.x : (w == 1 ? blk.y : (w == 2 ? blk.z : blk.w));
+    }
+};
+
+// Rounding of one operation result to the propensity / uniform type.
+template <int PREC, int SR>
+struct Rounder {
+    using T = ModeTraits<PREC>;
+    SRBits bits;
+    __device__ __forceinline__ typename T::P rnd(typename T::P x, int op)
+    {
+        if constexpr (T::k16) {
+            if constexpr (SR) return sr16<T::kFmt>(x, bits.word(op), (op & 1) != 0);
+            else return rn16<T::kFmt>(x);
+        } else {
+            return x;
+        }
+    }
+};
+
+// ---------------------------------------------------------- compile-time loops
+template <int... Is, class F>
+__device__ __forceinline__ void unroll_impl(std::integer_sequence<int, Is...>, F &&f)
+{
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void unroll(F &&f)
+{
+    unroll_impl(std::make_integer_sequence<int, N>{}, static_cast<F &&>(f));
+}
+
+// ------------------------------------------------------------- model policies
+// A structure description S provides N, M and constexpr tables ord, nu, lw,
+// hh (Hill exponent), hreg (regulator) and cs (constant species).  Every
+// accessor is forced to a compile-time constant through integral_constant.
+template <class S, bool NORM>
+struct StaticCounts {
+    __host__ __device__ static constexpr int chain_ops(int j)
+    {
+        if (S::lw[j] == 1) return S::hh[j] + 3;
+        int ops = 0;
+        for (int i = 0; i < S::N; ++i)
+            if (!(NORM && S::cs[i] && S::ord[j][i] > 0)) ops += 2 * S::ord[j][i];
+        return ops;
+    }
+    __host__ __device__ static constexpr int chain_start(int j)
+    {
+        int s = 0;
+        for (int q = 0; q < j; ++q) s += chain_ops(q);
+        return s;
+    }
+};
+
+template <class S, bool NORM>
+struct StaticModel {
+    using C = StaticCounts<S, NORM>;
+    static constexpr int N = S::N;
+    static constexpr int M = S::M;
+    template <int J> __device__ static constexpr bool active(const RunArgs &) { return true; }
+    template <int J, int I> __device__ static constexpr int order(const RunArgs &)
+    {
+        return std::integral_constant<int, S::ord[J][I]>::value;
+    }
+    template <int J, int I> __device__ static constexpr int nu(const RunArgs &)
+    {
+        return std::integral_constant<int, S::cs[I] ? 0 : S::nu[J][I]>::value;
+    }
+    template <int J, int I> __device__ static constexpr bool folded(const RunArgs &)
+    {
+        return std::integral_constant<bool, (NORM && S::cs[I] && S::ord[J][I] > 0)>::value;
+    }
+    template <int J> __device__ static constexpr int law(const RunArgs &) { return std::integral_constant<int, S::lw[J]>::value; }
+    template <int J> __device__ static constexpr int hill_h(const RunArgs &) { return std::integral_constant<int, S::hh[J]>::value; }
+    template <int J> __device__ static constexpr int hill_reg(const RunArgs &) { return std::integral_constant<int, S::hreg[J]>::value; }
+    template <int J> __device__ static constexpr int chain_start(const RunArgs &)
+    {
+        return std::integral_constant<int, C::chain_start(J)>::value;
+    }
+    __device__ static constexpr int total_chain_ops(const RunArgs &)
+    {
+        return std::integral_constant<int, C::chain_start(M)>::value;
+    }
+    __device__ static constexpr int last(const RunArgs &) { return M - 1; }
+};
+
+// General kernel: structure from the kernel arguments, bounded by kMaxN/kMaxM.
+struct GeneralModel {
+    static constexpr int N = kMaxN;
+    static constexpr int M = kMaxM;
+    template <int J> __device__ static bool active(const RunArgs &a) { return J < a.M; }
+    template <int J, int I> __device__ static int order(const RunArgs &a) { return a.order[J][I]; }
+    template <int J, int I> __device__ static int nu(const RunArgs &a) { return a.stoich[J][I]; }
+    template <int J, int I> __device__ static bool folded(const RunArgs &a) { return a.folded[J][I] != 0; }
+    template <int J> __device__ static int law(const RunArgs &a) { return a.law[J]; }
+    template <int J> __device__ static int hill_h(const RunArgs &a) { return a.hill_h[J]; }
+    template <int J> __device__ static int hill_reg(const RunArgs &a) { return a.hill_reg[J]; }
+    template <int J> __device__ static int chain_start(const RunArgs &a) { return a.chain_start[J]; }
+    __device__ static int total_chain_ops(const RunArgs &a) { return a.sr_ops; }
+    __device__ static int last(const RunArgs &a) { return a.M - 1; }
+};
+
+// --------------------------------------------------------------- lane state
+template <class Model, int PREC>
+struct Lane {
+    using Tr = ModeTraits<PREC>;
+    using P = typename Tr::P;
+    int x[Model::N];
+    P c[Model::M];       // c'_j in the propensity type
+    P h0[Model::M];      // alpha0 (Hill rows)
+    P h1[Model::M];      // alpha  (Hill rows)
+    P t;
+    P s_next;            // next sample time (or +inf)
+    int64_t n;           // events fired
+    int64_t item;        // work item
+    uint32_t traj;       // global trajectory id
+    int k;               // next snapshot
+    uint32_t status;
+    bool active;
+};
+
+template <int PREC>
+__device__ __forceinline__ typename ModeTraits<PREC>::P to_time(double v)
+{
+    using Tr = ModeTraits<PREC>;
+    if constexpr (Tr::kF64) return v;
+    else if constexpr (Tr::kUniform) return rn16<Tr::kFmt>((float)v);
+    else return (float)v;
+}
+
+template <int PREC>
+__device__ __forceinline__ typename ModeTraits<PREC>::P to_prop(double v)
+{
+    using Tr = ModeTraits<PREC>;
+    if constexpr (Tr::kF64) return v;
+    else if constexpr (Tr::k16) return rn16<Tr::kFmt>((float)v);
+    else return (float)v;
+}
+
+template <int PREC>
+__device__ __forceinline__ bool is_nan(typename ModeTraits<PREC>::P v) { return v != v; }
+
+// --------------------------------------------------------------- snapshots
+template <class Model>
+__device__ __forceinline__ void store_state(const RunArgs &a, int k, int64_t item, const int *x, uint32_t &status)
+{
+    const int64_t col = item;
+    const int64_t stride = a.n_traj;
+    unroll<Model::N>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (i < a.N) {
+            const int64_t idx = ((int64_t)k * a.N + i) * stride + col;
+            int v = x[i];
+            if (a.state_bytes == 2) {
+                if (v > 32767) { v = 32767; status |= ST_STATE_RANGE; }
+                if (v < -32768) { v = -32768; status |= ST_STATE_RANGE; }
+                static_cast<int16_t *>(a.out)[idx] = (int16_t)v;
+            } else {
+                static_cast<int32_t *>(a.out)[idx] = v;
+            }
+        }
+    });
+}
+
+template <class Model, int PREC>
+__device__ void finish(const RunArgs &a, Lane<Model, PREC> &L)
+{
+    while (L.k < a.K) {
+        store_state<Model>(a, L.k, L.item, L.x, L.status);
+        L.k += 1;
+    }
+    a.status[L.item] = L.status;
+    if (a.n_events) a.n_events[L.item] = L.n;
+    if (a.t_final) a.t_final[L.item] = (double)L.t;
+    L.active = false;
+}
+
+// ------------------------------------------------------------ lane refill
+template <class Model, int PREC>
+__device__ void init_lane(const RunArgs &a, Lane<Model, PREC> &L, int64_t item, const typename ModeTraits<PREC>::P *smp)
+{
+    using P = typename ModeTraits<PREC>::P;
+    L.item = item;
+    L.traj = a.traj_offset + (uint32_t)item;
+    const int set = a.n_sets > 1 ? (int)(item / a.traj_per_set) : 0;
+    unroll<Model::N>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        L.x[i] = a.x0_tab ? a.x0_tab[(int64_t)set * a.N + i] : a.x0[i];
+    });
+    unroll<Model::M>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        if (Model::template active<j>(a)) {
+            const double c = a.n_sets > 1 ? a.cprime_tab[(int64_t)set * a.M + j] : a.cprime[j];
+            L.c[j] = to_prop<PREC>(c);
+            if (Model::template law<j>(a) == 1) {
+                const double g0 = (a.n_sets > 1 && a.hill_tab) ? a.hill_tab[((int64_t)set * a.M + j) * 2 + 0] : a.hill_a0[j];
+                const double g1 = (a.n_sets > 1 && a.hill_tab) ? a.hill_tab[((int64_t)set * a.M + j) * 2 + 1] : a.hill_a[j];
+                L.h0[j] = to_prop<PREC>(g0);
+                L.h1[j] = to_prop<PREC>(g1);
+            } else {
+                L.h0[j] = P(0);
+                L.h1[j] = P(0);
+            }
+        } else {
+            L.c[j] = P(0);
+            L.h0[j] = P(0);
+            L.h1[j] = P(0);
+        }
+    });
+    L.t = P(0);
+    L.n = 0;
+    L.k = 0;
+    L.status = 0;
+    L.s_next = a.K > 0 ? smp[0] : P(__int_as_float(0x7F800000));
+    L.active = true;
+}
+
+// ------------------------------------------------------------ one SSA step
+// Executes step n = L.n with uniform words (w0, w1).  Returns with L.active
+// cleared when the trajectory has finished (results written).
+template <class Model, int PREC, int SR>
+__device__ __forceinline__ void ssa_step(const RunArgs &a, Lane<Model, PREC> &L, uint32_t w0, uint32_t w1,
+                                         const typename ModeTraits<PREC>::P *smp, typename ModeTraits<PREC>::P t_end)
+{
+    using Tr = ModeTraits<PREC>;
+    using P = typename Tr::P;
+    constexpr int M = Model::M;
+
+    if (L.n >= a.max_events) {
+        L.status |= ST_MAX_EVENTS;
+        finish<Model, PREC>(a, L);
+        return;
+    }
+
+    Rounder<PREC, SR> R;
+    int sr_total = 0;
+    if constexpr (Tr::k16 && SR) {
+        sr_total = Model::total_chain_ops(a) + (Tr::kUniform ? (Model::last(a) + 5) : 0);
+        const int B = (sr_total + 7) >> 3;
+        R.bits.base = (uint64_t)L.n * (uint64_t)B;
+        R.bits.traj = L.traj;
+        R.bits.k0 = a.key0;
+        R.bits.k1 = a.key1;
+        R.bits.cur = -1;
+    }
+
+    // 1. propensities a_j (Sec. 2 step 1), in the propensity type
+    P prop[M];
+    unroll<M>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        prop[j] = P(0);
+        if (!Model::template active<j>(a)) return;
+        int op = Model::template chain_start<j>(a);
+        if (Model::template law<j>(a) == 1) {
+            const int reg = Model::template hill_reg<j>(a);
+            int xr = 0;
+            unroll<Model::N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                if (i == reg) xr = L.x[i];
+            });
+            const P Pv = R.rnd((P)xr, op++);
+            P q = Pv;
+            const int h = Model::template hill_h<j>(a);
+            for (int m = 1; m < h; ++m) q = R.rnd(q * Pv, op++);
+            const P d = R.rnd(P(1) + q, op++);
+            const P f = R.rnd(L.h1[j] / d, op++);
+            prop[j] = R.rnd(L.h0[j] + f, op++);
+        } else {
+            P av = L.c[j];
+            bool zero = false;
+            unroll<Model::N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const int r = Model::template order<j, i>(a);
+                if (r > 0 && !Model::template folded<j, i>(a)) {
+                    zero = zero || (L.x[i] < r);
+                    for (int m = 0; m < r; ++m) {
+                        const P f = R.rnd((P)(L.x[i] - m), op++);
+                        av = R.rnd(av * f, op++);
+                    }
+                }
+            });
+            prop[j] = zero ? P(0) : av;
+        }
+    });
+
+    // 2. partial sums S_j and a0 (Sec. 2 step 1; sensitive operation 1)
+    P S[M];
+    P a0 = P(0);
+    {
+        int op = Model::total_chain_ops(a);
+        unroll<M>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            if (!Model::template active<j>(a)) { S[j] = a0; return; }
+            if constexpr (j == 0) {
+                S[0] = prop[0];
+            } else {
+                if constexpr (Tr::kUniform) S[j] = R.rnd(S[j - 1] + prop[j], op++);
+                else S[j] = S[j - 1] + prop[j];
+            }
+            a0 = S[j];
+        });
+    }
+
+    // degenerate states (readings for a0 = NaN, inf, 0)
+    if (is_nan<PREC>(a0)) { L.status |= ST_NAN; finish<Model, PREC>(a, L); return; }
+    if (a0 == P(__int_as_float(0x7F800000))) { L.status |= ST_OVERFLOW; finish<Model, PREC>(a, L); return; }
+    if (a0 == P(0)) { finish<Model, PREC>(a, L); return; }
+
+    // 3. waiting time and selection target (Sec. 2 steps 2-3)
+    P tau, target, t_new;
+    if constexpr (Tr::kF64) {
+        const double u1 = ((double)w0 + 1.0) * 0x1p-32;
+        const double u2 = (double)w1 * 0x1p-32;
+        const double E = -log_f64(u1);
+        tau = E / a0;
+        target = u2 * a0;
+        t_new = L.t + tau;
+    } else {
+        const float u1 = (float)((w0 >> 8) + 1u) * 0x1p-24f;
+        const float u2 = (float)(w1 >> 8) * 0x1p-24f;
+        if constexpr (Tr::kUniform) {
+            int op = Model::total_chain_ops(a) + Model::last(a);
+            const float E = R.rnd(-log_f32(u1), op++);
+            const float U2 = R.rnd(u2, op++);
+            tau = R.rnd(E / a0, op++);
+            target = R.rnd(U2 * a0, op++);
+            t_new = R.rnd(L.t + tau, op++);
+        } else {
+            const float E = -log_f32(u1);
+            tau = E / a0;
+            target = u2 * a0;
+            t_new = L.t + tau;
+        }
+    }
+
+    // 4a. snapshots strictly before the event time
+    while (L.s_next < t_new) {
+        store_state<Model>(a, L.k, L.item, L.x, L.status);
+        L.k += 1;
+        L.s_next = L.k < a.K ? smp[L.k] : P(__int_as_float(0x7F800000));
+    }
+    if (t_new > t_end) { finish<Model, PREC>(a, L); return; }
+
+    // 4b. selection: smallest mu with S_mu > target; else last a_j > 0
+    int mu = -1;
+    unroll<M>([&](auto J) {
+        constexpr int j = M - 1 - decltype(J)::value;
+        if (Model::template active<j>(a) && S[j] > target) mu = j;
+    });
+    if (mu < 0) {
+        unroll<M>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            if (Model::template active<j>(a) && prop[j] > P(0)) mu = j;
+        });
+    }
+
+    // 4c. integer state update x += nu_mu, clock t = t_new
+    bool negative = false;
+    unroll<M>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        if (mu == j) {
+            unroll<Model::N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const int d = Model::template nu<j, i>(a);
+                if (d != 0) {
+                    L.x[i] += d;
+                    negative = negative || (L.x[i] < 0);
+                }
+            });
+        }
+    });
+    L.t = t_new;
+    L.n += 1;
+    if (negative) {
+        L.status |= ST_STATE_RANGE;
+        finish<Model, PREC>(a, L);
+    }
+}
+
+// ------------------------------------------------- one step, general model
+// Same contract as ssa_step, with the structure read from the kernel
+// arguments in runtime loops (state and tables in local memory).  Used for
+// networks that match no compiled structure.
+template <int PREC, int SR>
+__device__ __noinline__ void ssa_step_general(const RunArgs &a, Lane<GeneralModel, PREC> &L, uint32_t w0, uint32_t w1,
+                                              const typename ModeTraits<PREC>::P *smp,
+                                              typename ModeTraits<PREC>::P t_end)
+{
+    using Tr = ModeTraits<PREC>;
+    using P = typename Tr::P;
+    const P kInf = P(__int_as_float(0x7F800000));
+
+    if (L.n >= a.max_events) {
+        L.status |= ST_MAX_EVENTS;
+        finish<GeneralModel, PREC>(a, L);
+        return;
+    }
+    Rounder<PREC, SR> R;
+    if constexpr (Tr::k16 && SR) {
+        const int sr_total = a.sr_ops + (Tr::kUniform ? (a.M - 1 + 5) : 0);
+        R.bits.base = (uint64_t)L.n * (uint64_t)((sr_total + 7) >> 3);
+        R.bits.traj = L.traj;
+        R.bits.k0 = a.key0;
+        R.bits.k1 = a.key1;
+        R.bits.cur = -1;
+    }
+
+    // propensities
+    P prop[kMaxM];
+#pragma unroll 1
+    for (int j = 0; j < a.M; ++j) {
+        int op = a.chain_start[j];
+        if (a.law[j] == 1) {
+            const P Pv = R.rnd((P)L.x[a.hill_reg[j]], op++);
+            P q = Pv;
+            for (int m = 1; m < a.hill_h[j]; ++m) q = R.rnd(q * Pv, op++);
+            const P d = R.rnd(P(1) + q, op++);
+            const P f = R.rnd(L.h1[j] / d, op++);
+            prop[j] = R.rnd(L.h0[j] + f, op++);
+        } else {
+            P av = L.c[j];
+            bool zero = false;
+#pragma unroll 1
+            for (int i = 0; i < a.N; ++i) {
+                const int r = a.order[j][i];
+                if (r == 0 || a.folded[j][i]) continue;
+                zero = zero || (L.x[i] < r);
+                for (int m = 0; m < r; ++m) {
+                    const P f = R.rnd((P)(L.x[i] - m), op++);
+                    av = R.rnd(av * f, op++);
+                }
+            }
+            prop[j] = zero ? P(0) : av;
+        }
+    }
+    // partial sums
+    P S[kMaxM];
+    S[0] = prop[0];
+    {
+        int op = a.sr_ops;
+#pragma unroll 1
+        for (int j = 1; j < a.M; ++j) {
+            if constexpr (Tr::kUniform) S[j] = R.rnd(S[j - 1] + prop[j], op++);
+            else S[j] = S[j - 1] + prop[j];
+        }
+    }
+    const P a0 = S[a.M - 1];
+    if (is_nan<PREC>(a0)) { L.status |= ST_NAN; finish<GeneralModel, PREC>(a, L); return; }
+    if (a0 == kInf) { L.status |= ST_OVERFLOW; finish<GeneralModel, PREC>(a, L); return; }
+    if (a0 == P(0)) { finish<GeneralModel, PREC>(a, L); return; }
+
+    P tau, target, t_new;
+    if constexpr (Tr::kF64) {
+        const double u1 = ((double)w0 + 1.0) * 0x1p-32;
+        const double u2 = (double)w1 * 0x1p-32;
+        const double E = -log_f64(u1);
+        tau = E / a0;
+        target = u2 * a0;
+        t_new = L.t + tau;
+    } else {
+        const float u1 = (float)((w0 >> 8) + 1u) * 0x1p-24f;
+        const float u2 = (float)(w1 >> 8) * 0x1p-24f;
+        if constexpr (Tr::kUniform) {
+            int op = a.sr_ops + a.M - 1;
+            const float E = R.rnd(-log_f32(u1), op++);
+            const float U2 = R.rnd(u2, op++);
+            tau = R.rnd(E / a0, op++);
+            target = R.rnd(U2 * a0, op++);
+            t_new = R.rnd(L.t + tau, op++);
+        } else {
+            const float E = -log_f32(u1);
+            tau = E / a0;
+            target = u2 * a0;
+            t_new = L.t + tau;
+        }
+    }
+    while (L.s_next < t_new) {
+        store_state<GeneralModel>(a, L.k, L.item, L.x, L.status);
+        L.k += 1;
+        L.s_next = L.k < a.K ? smp[L.k] : kInf;
+    }
+    if (t_new > t_end) { finish<GeneralModel, PREC>(a, L); return; }
+
+    int mu = -1;
+#pragma unroll 1
+    for (int j = 0; j < a.M; ++j)
+        if (S[j] > target) { mu = j; break; }
+    if (mu < 0) {
+#pragma unroll 1
+        for (int j = a.M - 1; j >= 0; --j)
+            if (prop[j] > P(0)) { mu = j; break; }
+    }
+    bool negative = false;
+#pragma unroll 1
+    for (int i = 0; i < a.N; ++i) {
+        L.x[i] += a.stoich[mu][i];
+        negative = negative || (L.x[i] < 0);
+    }
+    L.t = t_new;
+    L.n += 1;
+    if (negative) {
+        L.status |= ST_STATE_RANGE;
+        finish<GeneralModel, PREC>(a, L);
+    }
+}
+
+// ------------------------------------------------------------- the kernel
+// Persistent: every lane loops { refill if idle; two steps per Philox block
+// of stream 0 } until the work queue is drained.
+template <class Model, int PREC, int SR>
+__global__ void __launch_bounds__(256) ssa_kernel(const __grid_constant__ RunArgs a)
+{
+    using Tr = ModeTraits<PREC>;
+    using P = typename Tr::P;
+    __shared__ P smp[kMaxK];
+    for (int k = threadIdx.x; k < a.K; k += blockDim.x) smp[k] = to_time<PREC>(a.samples[k]);
+    __syncthreads();
+    const P t_end = to_time<PREC>(a.t_end);
+
+    const unsigned lane = threadIdx.x & 31u;
+    Lane<Model, PREC> L;
+    L.active = false;
+    bool drained = false;
+    for (;;) {
+        const unsigned need = __ballot_sync(0xFFFFFFFFu, !L.active && !drained);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if ((int)lane == leader) base = atomicAdd(a.queue_head, (unsigned long long)__popc(need));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            if (!L.active && !drained) {
+                const unsigned long long item = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+                if (item < (unsigned long long)a.n_traj) init_lane<Model, PREC>(a, L, (int64_t)item, smp);
+                else drained = true;
+            }
+        }
+        if (__ballot_sync(0xFFFFFFFFu, L.active) == 0u) break;
+        // L.n is even for every active lane here: block n/2 holds steps n, n+1
+        const uint64_t blk = (uint64_t)(L.n >> 1);
+        const uint4 u = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), L.traj, 0u), a.key0, a.key1);
+        if constexpr (std::is_same<Model, GeneralModel>::value) {
+            if (L.active) ssa_step_general<PREC, SR>(a, L, u.x, u.y, smp, t_end);
+            if (L.active) ssa_step_general<PREC, SR>(a, L, u.z, u.w, smp, t_end);
+        } else {
+            if (L.active) ssa_step<Model, PREC, SR>(a, L, u.x, u.y, smp, t_end);
+            if (L.active) ssa_step<Model, PREC, SR>(a, L, u.z, u.w, smp, t_end);
+        }
+    }
+}
+
+}  // namespace ssa

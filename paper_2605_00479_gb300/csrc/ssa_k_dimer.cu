@@ -1,0 +1,13 @@
+// Kernel instantiations for the dimer structure family.
+#include "ssa_launch.h"
+#include "ssa_models.h"
+
+namespace ssa {
+
+cudaError_t launch_dimer(const RunArgs &a, int prec, int sr, int norm, LaunchConfig cfg, cudaStream_t s, int *grid)
+{
+    (void)norm;  // no constant species: folding never applies
+    return launch_family<StaticModel<models::Dimer, false>>(a, prec, sr, cfg, s, grid);
+}
+
+}  // namespace ssa

@@ -1,0 +1,63 @@
+// ssa_launch.h -- per-family kernel launchers (one translation unit each, so
+// the kernel instantiations compile in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ssa_device.cuh"
+
+namespace ssa {
+
+struct LaunchConfig {
+    int block;          // threads per block (multiple of 32, <= 256)
+    int blocks_per_sm;  // 0: as many as occupancy allows
+};
+
+// Launch the persistent kernel of one family for precision `prec`, rounding
+// `sr` (0 RN, 1 SR) and `norm` (fold constant species).  Writes the grid size
+// used to *grid_out.  Returns the CUDA error of the launch.
+using Launcher = cudaError_t (*)(const RunArgs &a, int prec, int sr, int norm, LaunchConfig cfg,
+                                 cudaStream_t stream, int *grid_out);
+
+cudaError_t launch_general(const RunArgs &, int, int, int, LaunchConfig, cudaStream_t, int *);
+cudaError_t launch_birth_death(const RunArgs &, int, int, int, LaunchConfig, cudaStream_t, int *);
+cudaError_t launch_schlogl(const RunArgs &, int, int, int, LaunchConfig, cudaStream_t, int *);
+cudaError_t launch_telegraph(const RunArgs &, int, int, int, LaunchConfig, cudaStream_t, int *);
+cudaError_t launch_dimer(const RunArgs &, int, int, int, LaunchConfig, cudaStream_t, int *);
+cudaError_t launch_repressilator(const RunArgs &, int, int, int, LaunchConfig, cudaStream_t, int *);
+
+// Shared launch logic: choose the kernel for (prec, sr), size the grid from
+// occupancy (persistent: enough lanes to fill the GPU, no more than the work).
+template <class ModelF>
+cudaError_t launch_family(const RunArgs &a, int prec, int sr, LaunchConfig cfg, cudaStream_t stream, int *grid_out)
+{
+    using K = void (*)(const RunArgs);
+    K k = nullptr;
+    switch (prec) {
+    case FP64: k = ssa_kernel<ModelF, FP64, 0>; break;
+    case FP32: k = ssa_kernel<ModelF, FP32, 0>; break;
+    case MIXED_F16: k = sr ? ssa_kernel<ModelF, MIXED_F16, 1> : ssa_kernel<ModelF, MIXED_F16, 0>; break;
+    case MIXED_BF16: k = sr ? ssa_kernel<ModelF, MIXED_BF16, 1> : ssa_kernel<ModelF, MIXED_BF16, 0>; break;
+    case UNIFORM_F16: k = sr ? ssa_kernel<ModelF, UNIFORM_F16, 1> : ssa_kernel<ModelF, UNIFORM_F16, 0>; break;
+    case UNIFORM_BF16: k = sr ? ssa_kernel<ModelF, UNIFORM_BF16, 1> : ssa_kernel<ModelF, UNIFORM_BF16, 0>; break;
+    default: return cudaErrorInvalidValue;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, cfg.block, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;
+    long long grid = (long long)sms * per_sm;
+    const long long need = (a.n_traj + cfg.block - 1) / cfg.block;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    *grid_out = (int)grid;
+    k<<<(unsigned)grid, (unsigned)cfg.block, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ssa

@@ -1,0 +1,181 @@
+"""Python binding of the C ABI in include/ssa.h (argument marshalling only).
+
+Every step of the simulation runs in the CUDA kernels of libssa_gb300.so;
+this module converts Python/numpy/torch arguments into pointers and sizes.
+PyTorch supplies device memory and streams.  If the library has not been
+built, ``lib()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libssa_gb300.so")
+
+PRECISION = {"fp64": 0, "fp32": 1, "mixed_f16": 2, "mixed_bf16": 3, "uniform_f16": 4, "uniform_bf16": 5}
+ROUNDING = {"rn": 0, "sr": 1}
+STATUS_OVERFLOW, STATUS_MAX_EVENTS, STATUS_STATE_RANGE, STATUS_NAN = 1, 2, 4, 8
+SSA_OK, SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_ETIMEDOUT = 0, -1, -2, -3, -4
+FAMILIES = {0: "general", 1: "birth_death", 2: "schlogl", 3: "telegraph", 4: "dimer", 5: "repressilator"}
+
+# name -> (restype, argtypes) for every function declared in include/ssa.h
+_P = ctypes.c_void_p
+_I, _I64, _U64, _D = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+_RUN_ARGS = [_P, _I64, _U64, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, _P, _P, _P, _P, _P]
+SIGNATURES = {
+    "ssa_model_create": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "ssa_model_destroy": (None, [_P]),
+    "ssa_model_kernel_family": (_I, [_P]),
+    "ssa_ensemble_run": (_I, _RUN_ARGS),
+    "ssa_ensemble_run_host": (_I, _RUN_ARGS),
+    "ssa_set_launch_config": (_I, [_I, _I]),
+    "ssa_last_error": (ctypes.c_char_p, []),
+}
+
+_LIB = None
+
+
+class SSAError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"ssa error {code}: {message}")
+        self.code = code
+
+
+def lib():
+    """Load the CUDA engine.  Raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA engine not built ({LIB_PATH} missing): run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc != SSA_OK:
+        raise SSAError(rc, lib().ssa_last_error().decode())
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(_P)
+
+
+def _dev_ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Model:
+    """A reaction network (Sec. 2 problem statement), owned by the library."""
+
+    def __init__(self, order, stoich, rate, law=None, hill=None, constant=None):
+        self.order = np.ascontiguousarray(order, dtype=np.int32)
+        M, N = self.order.shape
+        self.N, self.M = N, M
+        self.stoich = np.ascontiguousarray(stoich, dtype=np.int32).reshape(M, N)
+        self.rate = np.ascontiguousarray(rate, dtype=np.float64).reshape(M)
+        self.law = None if law is None else np.ascontiguousarray(law, dtype=np.int32)
+        self.hill = None if hill is None else np.ascontiguousarray(hill, dtype=np.float64).reshape(M, 4)
+        self.constant = None if constant is None else np.ascontiguousarray(constant, dtype=np.uint8)
+        h = _P()
+        _check(lib().ssa_model_create(N, M, _np_ptr(self.order), _np_ptr(self.stoich), _np_ptr(self.rate),
+                                      _np_ptr(self.law), _np_ptr(self.hill), _np_ptr(self.constant), ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_dict(cls, m):
+        return cls(m["order"], m["stoich"], m["rate"], m.get("law"), m.get("hill"), m.get("constant"))
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def family(self):
+        return FAMILIES[lib().ssa_model_kernel_family(self._h)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ssa_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_launch_config(threads_per_block=128, blocks_per_sm=0):
+    """Launch shape for later runs (speed only; results do not depend on it)."""
+    _check(lib().ssa_set_launch_config(int(threads_per_block), int(blocks_per_sm)))
+
+
+def _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision, rounding, normalise, seed,
+                 max_events, state_bytes):
+    x0 = np.ascontiguousarray(x0, dtype=np.int32)
+    st = np.ascontiguousarray(np.atleast_1d(sample_times), dtype=np.float64)
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    rnd = ROUNDING[rounding] if isinstance(rounding, str) else int(rounding)
+    return x0, st, prec, rnd
+
+
+def ensemble_run(model, n_traj, x0, t_end, sample_times, precision="fp64", rounding="rn", normalise=False, seed=0,
+                 max_events=10**9, state_bytes=4, out=None, status=None, n_events=None, t_final=None,
+                 stream=None, traj_offset=0, with_events=True, with_t_final=True):
+    """Launch ssa_ensemble_run on CUDA tensors (allocated here when None).
+
+    Returns a dict of device tensors: snapshots [K, N, n_traj], status,
+    n_events, t_final.  Asynchronous on ``stream`` (a torch.cuda.Stream or
+    None for the current stream)."""
+    import torch
+    x0, st, prec, rnd = _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision, rounding,
+                                     normalise, seed, max_events, state_bytes)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    K = st.size
+    if out is None:
+        out = torch.empty((K, model.N, n_traj), dtype=torch.int16 if state_bytes == 2 else torch.int32, device=dev)
+    if status is None:
+        status = torch.empty(n_traj, dtype=torch.int32, device=dev)
+    if n_events is None and with_events:
+        n_events = torch.empty(n_traj, dtype=torch.int64, device=dev)
+    if t_final is None and with_t_final:
+        t_final = torch.empty(n_traj, dtype=torch.float64, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().ssa_ensemble_run(model.handle, int(n_traj), int(traj_offset), _np_ptr(x0), float(t_end), K,
+                                  _np_ptr(st), prec, rnd, int(bool(normalise)), int(seed) & (2**64 - 1),
+                                  int(max_events), int(state_bytes), _dev_ptr(out), _dev_ptr(status),
+                                  _dev_ptr(n_events), _dev_ptr(t_final), ctypes.c_void_p(s.cuda_stream)))
+    return {"snapshots": out, "status": status, "n_events": n_events, "t_final": t_final}
+
+
+def ensemble_run_host(model, n_traj, x0, t_end, sample_times, precision="fp64", rounding="rn", normalise=False,
+                      seed=0, max_events=10**9, state_bytes=4, out=None, status=None, n_events=None, t_final=None,
+                      stream=None, traj_offset=0):
+    """ssa_ensemble_run_host: host (numpy) outputs; synchronous."""
+    x0, st, prec, rnd = _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision, rounding,
+                                     normalise, seed, max_events, state_bytes)
+    K = st.size
+    if out is None:
+        out = np.empty((K, model.N, n_traj), dtype=np.int16 if state_bytes == 2 else np.int32)
+    if status is None:
+        status = np.empty(n_traj, dtype=np.uint32)
+    if n_events is None:
+        n_events = np.empty(n_traj, dtype=np.int64)
+    if t_final is None:
+        t_final = np.empty(n_traj, dtype=np.float64)
+    sp = None
+    if stream is not None:
+        sp = ctypes.c_void_p(stream.cuda_stream)
+    _check(lib().ssa_ensemble_run_host(model.handle, int(n_traj), int(traj_offset), _np_ptr(x0), float(t_end), K,
+                                       _np_ptr(st), prec, rnd, int(bool(normalise)), int(seed) & (2**64 - 1),
+                                       int(max_events), int(state_bytes), _np_ptr(out), _np_ptr(status),
+                                       _np_ptr(n_events), _np_ptr(t_final), sp))
+    return {"snapshots": out, "status": status, "n_events": n_events, "t_final": t_final}

@@ -1,0 +1,114 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads,
+exports every function include/ssa.h declares, and rejects invalid arguments
+on the host before anything is launched."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2605_00479_gb300 import presets as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ssa():
+    from paper_2605_00479_gb300 import build, ssa as mod
+    build.build()
+    return mod
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "ssa.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ssa_\w+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_function(ssa):
+    names = declared_functions()
+    assert len(names) >= 7
+    L = ctypes.CDLL(ssa.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in ssa.SIGNATURES, n
+
+
+def test_structure_families(ssa):
+    assert ssa.Model.from_dict(P.birth_death()).family == "birth_death"
+    assert ssa.Model.from_dict(P.schlogl()).family == "schlogl"
+    assert ssa.Model.from_dict(P.telegraph()).family == "telegraph"
+    assert ssa.Model.from_dict(P.dimer()).family == "dimer"
+    assert ssa.Model.from_dict(P.repressilator()).family == "repressilator"
+    assert ssa.Model.from_dict(P.repressilator(h=3)).family == "general"
+    assert ssa.Model.from_dict(P.hill_self()).family == "general"
+
+
+@pytest.mark.parametrize("bad", ["order", "N", "M", "hill_h", "hill_reg", "rate_nan", "rate_neg", "law"])
+def test_model_create_rejects(ssa, bad):
+    m = {k: (None if v is None else np.array(v, copy=True)) for k, v in P.repressilator().items() if k != "names"}
+    order, stoich = m["order"], m["stoich"]
+    if bad == "order":
+        order[1, 0] = 4
+    elif bad == "N":
+        order, stoich = np.zeros((2, 9), np.int32), np.zeros((2, 9), np.int32)
+        m["rate"], m["law"], m["hill"] = np.ones(2), None, None
+    elif bad == "M":
+        order, stoich = np.zeros((17, 1), np.int32), np.zeros((17, 1), np.int32)
+        m["rate"], m["law"], m["hill"] = np.ones(17), None, None
+    elif bad == "hill_h":
+        m["hill"][0, 2] = 0
+    elif bad == "hill_reg":
+        m["hill"][0, 3] = 6
+    elif bad == "rate_nan":
+        m["rate"][1] = np.nan
+    elif bad == "rate_neg":
+        m["rate"][1] = -1.0
+    elif bad == "law":
+        m["law"][1] = 7
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.Model(order, stoich, m["rate"], m["law"], m["hill"])
+    assert e.value.code == ssa.SSA_EINVAL
+
+
+@pytest.mark.parametrize("case", ["precision", "sr_fp64", "t_end", "unsorted", "beyond", "no_samples", "state_bytes",
+                                  "max_events", "ids", "x0"])
+def test_run_rejects_before_launch(ssa, case):
+    m = ssa.Model.from_dict(P.birth_death())
+    kw = dict(n_traj=4, x0=[0], t_end=10.0, sample_times=[0.0, 5.0, 10.0], precision="fp32", rounding="rn",
+              seed=0, max_events=100, state_bytes=4, traj_offset=0)
+    if case == "precision":
+        kw["precision"] = 9
+    elif case == "sr_fp64":
+        kw["precision"], kw["rounding"] = "fp64", "sr"
+    elif case == "t_end":
+        kw["t_end"] = 0.0
+    elif case == "unsorted":
+        kw["sample_times"] = [5.0, 1.0]
+    elif case == "beyond":
+        kw["sample_times"] = [11.0]
+    elif case == "no_samples":
+        kw["sample_times"] = []
+    elif case == "state_bytes":
+        kw["state_bytes"] = 3
+    elif case == "max_events":
+        kw["max_events"] = -1
+    elif case == "ids":
+        kw["traj_offset"] = 2**32 - 2
+    elif case == "x0":
+        kw["x0"] = [-1]
+    out = np.zeros(12, np.int32)
+    st = np.zeros(4, np.uint32)
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.ensemble_run_host(m, out=out.reshape(-1, 1, 4)[:max(1, len(kw["sample_times"]))] if kw["sample_times"] else None,
+                              status=st, **kw)
+    assert e.value.code == ssa.SSA_EINVAL
+
+
+def test_launch_config_validation(ssa):
+    with pytest.raises(ssa.SSAError):
+        ssa.set_launch_config(48, 0)
+    with pytest.raises(ssa.SSAError):
+        ssa.set_launch_config(512, 0)
+    ssa.set_launch_config(128, 0)

@@ -372,7 +372,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-traj", type=int, default=None,
+                    help="trajectories per GPU (default 10^6; smaller values are for profiling only)")
+    ap.add_argument("--modes", default=None, help="comma list like mixed_f16:rn (profiling only)")
     args = ap.parse_args()
+    global N_TRAJ, MODES16
+    if args.n_traj:
+        N_TRAJ = args.n_traj
+    if args.modes:
+        MODES16 = [tuple(m.split(":")) for m in args.modes.split(",")]
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -161,11 +161,77 @@ int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_
  *   threads_per_block  multiple of 32 in 32..256
  *   blocks_per_sm      resident blocks per SM to launch (0 = as many as the
  *                      occupancy calculator allows)
+ *   slice_pairs        pairs of steps each lane runs between two checks for
+ *                      finished lanes to refill, 1..64
  * Results never depend on the launch shape; only speed does.  Not
  * synchronised with concurrent launches from other threads.
  * Errors: SSA_EINVAL.
  */
-int ssa_set_launch_config(int threads_per_block, int blocks_per_sm);
+int ssa_set_launch_config(int threads_per_block, int blocks_per_sm, int slice_pairs);
+
+/*
+ * Batched heterogeneous runs: several groups, each a model with a sweep of
+ * parameter sets, simulated by ONE persistent kernel with one device work
+ * queue per group.  Lanes that finish a trajectory take the next one from
+ * their warp's current group; a warp moves to the next group once it has
+ * drained the current one.  All groups share t_end, the sample times, the
+ * precision, rounding, normalisation, seed, event cap and state storage.
+ *
+ * ssa_batch_group:
+ *   model         the network (its structure; its rates are defaults)
+ *   n_sets        parameter sets, >= 1
+ *   traj_per_set  trajectories per set, >= 0; item r of the group belongs to
+ *                 set r / traj_per_set and has global trajectory id
+ *                 traj_offset + r (ids must fit in 32 bits)
+ *   rates         host [n_sets][M] c-convention rates, or NULL (model's)
+ *   hill          host [n_sets][M][2] {alpha0, alpha} for Hill rows, or NULL
+ *   x0            host [n_sets][N] initial counts
+ *   out           device [K][N][n_sets * traj_per_set]
+ *   traj_status   device [n_sets * traj_per_set]
+ *   n_events      device [n_sets * traj_per_set] or NULL
+ *   t_final       device [n_sets * traj_per_set] or NULL
+ * Results of every trajectory equal those of ssa_ensemble_run with the same
+ * rates, x0 and global trajectory id.
+ */
+typedef struct {
+    const ssa_model *model;
+    int64_t n_sets;
+    int64_t traj_per_set;
+    const double *rates;
+    const double *hill;
+    const int32_t *x0;
+    uint64_t traj_offset;
+    void *out;
+    uint32_t *traj_status;
+    int64_t *n_events;
+    double *t_final;
+} ssa_batch_group;
+
+typedef struct ssa_batch ssa_batch;   /* opaque, owned by the library */
+
+/* Validate the groups, compute every set's c' in binary64, upload the
+ * per-set tables to device memory owned by the batch (synchronous).
+ * n_groups in 1..16.  Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA. */
+int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, int n_samples,
+                     const double *sample_times, int precision, int rounding, int normalise,
+                     uint64_t seed, int64_t max_events, int state_bytes, ssa_batch **out);
+
+/* Run the whole batch on `stream`.  On a non-NULL stream the queue reset and
+ * the kernel are captured once into a CUDA graph and replayed on later calls;
+ * on the NULL stream they are launched directly.  Asynchronous. */
+int ssa_batch_launch(ssa_batch *batch, void *stream);
+
+/* Pick threads per block, resident blocks per SM and step pairs per refill
+ * check by timing short runs of this batch (at most 2 lanes' worth of
+ * trajectories per lane, events capped at 4096 per trajectory).  Writes
+ * provisional results into the output buffers; launch again afterwards.
+ * Synchronous.  Any of the out pointers may be NULL. */
+int ssa_batch_autotune(ssa_batch *batch, void *stream, int *threads_per_block, int *blocks_per_sm,
+                       int *slice_pairs, double *best_ms);
+
+/* Release the batch and its device memory (NULL is allowed).  No launch of
+ * it may still be running. */
+void ssa_batch_destroy(ssa_batch *batch);
 
 /* Thread-local description of the last error on the calling thread. */
 const char *ssa_last_error(void);

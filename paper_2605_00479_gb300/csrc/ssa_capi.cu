@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/ssa.h"
 #include "ssa_launch.h"
@@ -49,7 +50,7 @@ int cuda_fail(cudaError_t e, const char *what)
     return fail(SSA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-ssa::LaunchConfig g_cfg = {128, 0};
+ssa::LaunchConfig g_cfg = {128, 0, 1};
 
 template <class S>
 bool matches(const ssa_model &m)
@@ -189,13 +190,15 @@ extern "C" {
 
 const char *ssa_last_error(void) { return g_last_error.c_str(); }
 
-int ssa_set_launch_config(int threads_per_block, int blocks_per_sm)
+int ssa_set_launch_config(int threads_per_block, int blocks_per_sm, int slice_pairs)
 {
     if (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32 != 0)
         return fail(SSA_EINVAL, "threads_per_block must be a multiple of 32 in 32..256");
     if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(SSA_EINVAL, "blocks_per_sm must be in 0..64");
+    if (slice_pairs < 1 || slice_pairs > 64) return fail(SSA_EINVAL, "slice_pairs must be in 1..64");
     g_cfg.block = threads_per_block;
     g_cfg.blocks_per_sm = blocks_per_sm;
+    g_cfg.slice_pairs = slice_pairs;
     return SSA_OK;
 }
 
@@ -276,6 +279,8 @@ int ssa_ensemble_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offse
     fill_structure(*model, normalise, x0, *a);
     a->K = n_samples;
     a->n_traj = n_traj;
+    a->n_work = n_traj;
+    a->slice_pairs = g_cfg.slice_pairs;
     a->traj_offset = (uint32_t)traj_offset;
     a->n_sets = 1;
     a->traj_per_set = n_traj;
@@ -354,5 +359,321 @@ int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_
     if (rc == SSA_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
     return rc;
 }
+
+}  // extern "C"
+
+// ======================================================================
+// Batched heterogeneous runs
+// ======================================================================
+struct ssa_batch {
+    int n_groups;
+    int precision, rounding, normalise;
+    bool compact;
+    int64_t work;
+    ssa::LaunchConfig cfg;
+    char *dmem;
+    size_t dmem_bytes;
+    ssa::RunArgs *d_groups;
+    ssa::RunArgs *d_tune_groups;
+    unsigned long long *d_heads;
+    ssa::RunArgs *h_groups;   // host copies [n_groups]
+    ssa::BatchArgs *args;
+    cudaGraphExec_t exec;
+    bool graph_valid;
+};
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Device bytes of one group's per-set tables: c' [S][M] f64, Hill amplitudes
+// [S][M][2] f64, x0 [S][N] i32, each 256-byte aligned.  Used both to size
+// the arena and to place the tables in it.
+struct GroupTables {
+    size_t cprime, hill, x0;
+    size_t total() const { return cprime + hill + x0; }
+};
+
+GroupTables group_tables(int64_t n_sets, int M, int N)
+{
+    GroupTables t;
+    t.cprime = align_up(sizeof(double) * (size_t)n_sets * (size_t)M, 256);
+    t.hill = align_up(sizeof(double) * 2 * (size_t)n_sets * (size_t)M, 256);
+    t.x0 = align_up(sizeof(int32_t) * (size_t)n_sets * (size_t)N, 256);
+    return t;
+}
+
+void batch_free(ssa_batch *b)
+{
+    if (!b) return;
+    if (b->graph_valid) cudaGraphExecDestroy(b->exec);
+    if (b->dmem) cudaFree(b->dmem);
+    delete[] b->h_groups;
+    delete b->args;
+    delete b;
+}
+
+cudaError_t batch_enqueue(ssa_batch *b, const ssa::BatchArgs &args, ssa::LaunchConfig cfg, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_heads, 0, sizeof(unsigned long long) * (size_t)b->n_groups, s);
+    if (e != cudaSuccess) return e;
+    int grid = 0;
+    return ssa::launch_batch(args, b->work, b->precision, b->rounding, b->compact, cfg, s, &grid);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, int n_samples,
+                     const double *sample_times, int precision, int rounding, int normalise, uint64_t seed,
+                     int64_t max_events, int state_bytes, ssa_batch **out)
+{
+    if (!out) return fail(SSA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_groups < 1 || n_groups > ssa::kMaxGroups) return fail(SSA_EINVAL, "n_groups must be in 1..%d", ssa::kMaxGroups);
+    if (!groups) return fail(SSA_EINVAL, "groups is NULL");
+    // table sizes, validation
+    size_t bytes = align_up(sizeof(ssa::RunArgs) * (size_t)n_groups, 256) * 2 + 256;
+    int64_t work = 0;
+    bool compact = true;
+    for (int g = 0; g < n_groups; ++g) {
+        const ssa_batch_group &G = groups[g];
+        if (!G.model) return fail(SSA_EINVAL, "group %d: model is NULL", g);
+        if (G.n_sets < 1 || G.traj_per_set < 0) return fail(SSA_EINVAL, "group %d: n_sets >= 1 and traj_per_set >= 0", g);
+        if (!G.x0) return fail(SSA_EINVAL, "group %d: x0 is NULL", g);
+        const int64_t items = G.n_sets * G.traj_per_set;
+        for (int64_t q = 0; q < G.n_sets; ++q) {
+            const int rc = validate_run(G.model, items, G.traj_offset, G.x0 + q * G.model->N, t_end, n_samples,
+                                        sample_times, precision, rounding, max_events, state_bytes);
+            if (rc != SSA_OK) return fail(rc, "group %d, set %lld: %s", g, (long long)q, g_last_error.c_str());
+            if (G.rates)
+                for (int j = 0; j < G.model->M; ++j) {
+                    const double c = G.rates[q * G.model->M + j];
+                    if (G.model->law[j] == SSA_LAW_MASS_ACTION && (!finite_double(c) || c < 0.0))
+                        return fail(SSA_EINVAL, "group %d, set %lld: rate %d must be finite and >= 0", g, (long long)q, j);
+                }
+            if (G.hill)
+                for (int j = 0; j < G.model->M; ++j)
+                    for (int c = 0; c < 2; ++c) {
+                        const double v = G.hill[(q * G.model->M + j) * 2 + c];
+                        if (G.model->law[j] == SSA_LAW_HILL_REPRESSION && (!finite_double(v) || v < 0.0))
+                            return fail(SSA_EINVAL, "group %d, set %lld: Hill amplitudes must be finite and >= 0", g, (long long)q);
+                    }
+        }
+        if (items > 0 && (!G.out || !G.traj_status)) return fail(SSA_EINVAL, "group %d: out and traj_status are required", g);
+        const int fam = G.model->family;
+        if (fam < 3) compact = false;
+        work += items;
+        bytes += group_tables(G.n_sets, G.model->M, G.model->N).total();
+    }
+    ssa_batch *b = new (std::nothrow) ssa_batch;
+    if (!b) return fail(SSA_ENOMEM, "out of host memory");
+    std::memset(b, 0, sizeof(*b));
+    b->n_groups = n_groups;
+    b->precision = precision;
+    b->rounding = rounding;
+    b->normalise = normalise ? 1 : 0;
+    b->compact = compact;
+    b->work = work;
+    b->cfg = g_cfg;
+    b->h_groups = new (std::nothrow) ssa::RunArgs[n_groups];
+    b->args = new (std::nothrow) ssa::BatchArgs;
+    if (!b->h_groups || !b->args) {
+        batch_free(b);
+        return fail(SSA_ENOMEM, "out of host memory");
+    }
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->dmem), bytes);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return e == cudaErrorMemoryAllocation ? fail(SSA_ENOMEM, "batch tables: out of device memory")
+                                              : cuda_fail(e, "cudaMalloc");
+    }
+    b->dmem_bytes = bytes;
+    char *p = b->dmem;
+    b->d_groups = reinterpret_cast<ssa::RunArgs *>(p);
+    p += align_up(sizeof(ssa::RunArgs) * (size_t)n_groups, 256);
+    b->d_tune_groups = reinterpret_cast<ssa::RunArgs *>(p);
+    p += align_up(sizeof(ssa::RunArgs) * (size_t)n_groups, 256);
+    b->d_heads = reinterpret_cast<unsigned long long *>(p);
+    p += 256;
+
+    std::memset(b->args, 0, sizeof(*b->args));
+    b->args->n_groups = n_groups;
+    b->args->normalise = b->normalise;
+    b->args->K = n_samples;
+    b->args->t_end = t_end;
+    b->args->groups = b->d_groups;
+    for (int k = 0; k < n_samples; ++k) b->args->samples[k] = sample_times[k];
+
+    for (int g = 0; g < n_groups && e == cudaSuccess; ++g) {
+        const ssa_batch_group &G = groups[g];
+        const ssa_model &m = *G.model;
+        ssa::RunArgs &a = b->h_groups[g];
+        std::memset(&a, 0, sizeof(a));
+        fill_structure(m, normalise, G.x0, a);
+        const int64_t S = G.n_sets;
+        std::vector<double> cp((size_t)S * m.M), hl((size_t)S * m.M * 2);
+        for (int64_t q = 0; q < S; ++q) {
+            ssa_model mq = m;
+            if (G.rates)
+                for (int j = 0; j < m.M; ++j) mq.rate[j] = G.rates[q * m.M + j];
+            int8_t folded[ssa::kMaxM][ssa::kMaxN];
+            rate_constants(mq, G.x0 + q * m.N, normalise, &cp[(size_t)q * m.M], folded);
+            for (int j = 0; j < m.M; ++j) {
+                const bool hill = m.law[j] == SSA_LAW_HILL_REPRESSION;
+                hl[((size_t)q * m.M + j) * 2 + 0] = hill ? (G.hill ? G.hill[(q * m.M + j) * 2 + 0] : m.hill[j][0]) : 0.0;
+                hl[((size_t)q * m.M + j) * 2 + 1] = hill ? (G.hill ? G.hill[(q * m.M + j) * 2 + 1] : m.hill[j][1]) : 0.0;
+            }
+        }
+        const GroupTables T = group_tables(S, m.M, m.N);
+        if ((size_t)(p - b->dmem) + T.total() > b->dmem_bytes) {   // placement must stay inside the arena
+            batch_free(b);
+            return fail(SSA_EINVAL, "internal: batch table layout exceeds its arena");
+        }
+        double *d_cp = reinterpret_cast<double *>(p);
+        p += T.cprime;
+        double *d_hl = reinterpret_cast<double *>(p);
+        p += T.hill;
+        int32_t *d_x0 = reinterpret_cast<int32_t *>(p);
+        p += T.x0;
+        e = cudaMemcpy(d_cp, cp.data(), sizeof(double) * cp.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_hl, hl.data(), sizeof(double) * hl.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_x0, G.x0, sizeof(int32_t) * (size_t)S * m.N, cudaMemcpyHostToDevice);
+        a.K = n_samples;
+        a.n_traj = S * G.traj_per_set;
+        a.n_work = a.n_traj;
+        a.slice_pairs = b->cfg.slice_pairs;
+        a.traj_offset = (uint32_t)G.traj_offset;
+        a.n_sets = (int)S;
+        a.traj_per_set = G.traj_per_set > 0 ? G.traj_per_set : 1;
+        a.cprime_tab = d_cp;
+        a.hill_tab = d_hl;
+        a.x0_tab = d_x0;
+        a.t_end = t_end;
+        for (int k = 0; k < n_samples; ++k) a.samples[k] = sample_times[k];
+        a.key0 = (uint32_t)seed;
+        a.key1 = (uint32_t)(seed >> 32);
+        a.max_events = max_events;
+        a.out = G.out;
+        a.state_bytes = state_bytes;
+        a.status = G.traj_status;
+        a.n_events = G.n_events;
+        a.t_final = G.t_final;
+        a.queue_head = b->d_heads + g;
+        b->args->family[g] = (int8_t)m.family;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_groups, b->h_groups, sizeof(ssa::RunArgs) * (size_t)n_groups, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, "batch upload");
+    }
+    *out = b;
+    return SSA_OK;
+}
+
+int ssa_batch_launch(ssa_batch *b, void *stream)
+{
+    if (!b) return fail(SSA_EINVAL, "batch is NULL");
+    if (b->work == 0) return SSA_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (s == nullptr) {
+        e = batch_enqueue(b, *b->args, b->cfg, s);
+        return e == cudaSuccess ? SSA_OK : cuda_fail(e, "batch launch");
+    }
+    if (!b->graph_valid) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        const cudaError_t e1 = batch_enqueue(b, *b->args, b->cfg, s);
+        e = cudaStreamEndCapture(s, &graph);
+        if (e1 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e1, "batch capture");
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        b->graph_valid = true;
+    }
+    e = cudaGraphLaunch(b->exec, s);
+    return e == cudaSuccess ? SSA_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int ssa_batch_autotune(ssa_batch *b, void *stream, int *threads_per_block, int *blocks_per_sm, int *slice_pairs,
+                       double *best_ms)
+{
+    if (!b) return fail(SSA_EINVAL, "batch is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    // the same capped proxy workload for every candidate
+    const int64_t lanes = (int64_t)sms * 2048;
+    std::vector<ssa::RunArgs> tune(b->h_groups, b->h_groups + b->n_groups);
+    int64_t tune_work = 0;
+    for (auto &a : tune) {
+        a.n_work = a.n_traj < 2 * lanes / b->n_groups ? a.n_traj : 2 * lanes / b->n_groups;
+        if (a.max_events > 4096) a.max_events = 4096;
+        tune_work += a.n_work;
+    }
+    if (tune_work == 0) return SSA_OK;
+    const int blocks[] = {64, 128, 256};
+    const int per_sm[] = {0, 4, 2};
+    const int slices[] = {1, 4, 16};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    ssa::BatchArgs targs = *b->args;
+    targs.groups = b->d_tune_groups;
+    double best = 1e300;
+    ssa::LaunchConfig best_cfg = b->cfg;
+    for (int blk : blocks)
+        for (int ps : per_sm)
+            for (int sl : slices) {
+                for (auto &a : tune) a.slice_pairs = sl;
+                e = cudaMemcpyAsync(b->d_tune_groups, tune.data(), sizeof(ssa::RunArgs) * tune.size(),
+                                    cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                ssa::LaunchConfig cfg = {blk, ps, sl};
+                if (e == cudaSuccess) e = batch_enqueue(b, targs, cfg, s);   // warm
+                if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) e = batch_enqueue(b, targs, cfg, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return cuda_fail(e, "autotune run");
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    best_cfg = cfg;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cfg = best_cfg;
+    for (int g = 0; g < b->n_groups; ++g) b->h_groups[g].slice_pairs = best_cfg.slice_pairs;
+    e = cudaMemcpy(b->d_groups, b->h_groups, sizeof(ssa::RunArgs) * (size_t)b->n_groups, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune upload");
+    if (b->graph_valid) {
+        cudaGraphExecDestroy(b->exec);
+        b->graph_valid = false;
+    }
+    if (threads_per_block) *threads_per_block = best_cfg.block;
+    if (blocks_per_sm) *blocks_per_sm = best_cfg.blocks_per_sm;
+    if (slice_pairs) *slice_pairs = best_cfg.slice_pairs;
+    if (best_ms) *best_ms = best;
+    return SSA_OK;
+}
+
+void ssa_batch_destroy(ssa_batch *b) { batch_free(b); }
 
 }  // extern "C"

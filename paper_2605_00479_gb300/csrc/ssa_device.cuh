@@ -62,7 +62,9 @@ struct RunArgs {
     int8_t hill_reg[kMaxM];
     int16_t chain_start[kMaxM];        // first SR operation of each chain
     // work
-    int64_t n_traj;                    // work items
+    int64_t n_traj;                    // work items (output column count)
+    int64_t n_work;                    // items to simulate (n_traj, or fewer while tuning)
+    int slice_pairs;                   // step pairs between refill checks (>= 1)
     uint32_t traj_offset;              // global id of item 0
     int n_sets;                        // parameter sets
     int64_t traj_per_set;              // item r uses set r / traj_per_set
@@ -748,23 +750,21 @@ __device__ __noinline__ void ssa_step_general(const RunArgs &a, Lane<GeneralMode
     }
 }
 
-// ------------------------------------------------------------- the kernel
-// Persistent: every lane loops { refill if idle; two steps per Philox block
-// of stream 0 } until the work queue is drained.
+// ---------------------------------------------------------- the work loop
+// Persistent loop of one warp over one work queue: lanes that are idle take
+// the next items (one atomicAdd per warp), then every lane runs `slice_pairs`
+// pairs of steps (one Philox block of stream 0 per pair) before the next
+// refill check.  Returns once the queue is drained and every lane is idle,
+// so the caller may move the whole warp to another queue.
 template <class Model, int PREC, int SR>
-__global__ void __launch_bounds__(256) ssa_kernel(const __grid_constant__ RunArgs a)
+__device__ __forceinline__ void run_queue(const RunArgs &a, const typename ModeTraits<PREC>::P *smp,
+                                          typename ModeTraits<PREC>::P t_end)
 {
-    using Tr = ModeTraits<PREC>;
-    using P = typename Tr::P;
-    __shared__ P smp[kMaxK];
-    for (int k = threadIdx.x; k < a.K; k += blockDim.x) smp[k] = to_time<PREC>(a.samples[k]);
-    __syncthreads();
-    const P t_end = to_time<PREC>(a.t_end);
-
     const unsigned lane = threadIdx.x & 31u;
     Lane<Model, PREC> L;
     L.active = false;
     bool drained = false;
+    const int slice = a.slice_pairs > 0 ? a.slice_pairs : 1;
     for (;;) {
         const unsigned need = __ballot_sync(0xFFFFFFFFu, !L.active && !drained);
         if (need) {
@@ -774,21 +774,95 @@ __global__ void __launch_bounds__(256) ssa_kernel(const __grid_constant__ RunArg
             base = __shfl_sync(0xFFFFFFFFu, base, leader);
             if (!L.active && !drained) {
                 const unsigned long long item = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-                if (item < (unsigned long long)a.n_traj) init_lane<Model, PREC>(a, L, (int64_t)item, smp);
+                if (item < (unsigned long long)a.n_work) init_lane<Model, PREC>(a, L, (int64_t)item, smp);
                 else drained = true;
             }
         }
         if (__ballot_sync(0xFFFFFFFFu, L.active) == 0u) break;
-        // L.n is even for every active lane here: block n/2 holds steps n, n+1
-        const uint64_t blk = (uint64_t)(L.n >> 1);
-        const uint4 u = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), L.traj, 0u), a.key0, a.key1);
-        if constexpr (std::is_same<Model, GeneralModel>::value) {
-            if (L.active) ssa_step_general<PREC, SR>(a, L, u.x, u.y, smp, t_end);
-            if (L.active) ssa_step_general<PREC, SR>(a, L, u.z, u.w, smp, t_end);
-        } else {
-            if (L.active) ssa_step<Model, PREC, SR>(a, L, u.x, u.y, smp, t_end);
-            if (L.active) ssa_step<Model, PREC, SR>(a, L, u.z, u.w, smp, t_end);
+        for (int s = 0; s < slice; ++s) {
+            // L.n is even for every active lane here: block n/2 holds steps n, n+1
+            const uint64_t blk = (uint64_t)(L.n >> 1);
+            const uint4 u = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), L.traj, 0u), a.key0, a.key1);
+            if constexpr (std::is_same<Model, GeneralModel>::value) {
+                if (L.active) ssa_step_general<PREC, SR>(a, L, u.x, u.y, smp, t_end);
+                if (L.active) ssa_step_general<PREC, SR>(a, L, u.z, u.w, smp, t_end);
+            } else {
+                if (L.active) ssa_step<Model, PREC, SR>(a, L, u.x, u.y, smp, t_end);
+                if (L.active) ssa_step<Model, PREC, SR>(a, L, u.z, u.w, smp, t_end);
+            }
+            if (s + 1 < slice && __ballot_sync(0xFFFFFFFFu, L.active) == 0u) break;
         }
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void load_samples(const double *samples, int K, typename ModeTraits<PREC>::P *smp)
+{
+    for (int k = threadIdx.x; k < K; k += blockDim.x) smp[k] = to_time<PREC>(samples[k]);
+    __syncthreads();
+}
+
+// ------------------------------------------------------------- the kernels
+// One model, one queue: arguments in parameter space.
+template <class Model, int PREC, int SR>
+__global__ void __launch_bounds__(256) ssa_kernel(const __grid_constant__ RunArgs a)
+{
+    using P = typename ModeTraits<PREC>::P;
+    __shared__ P smp[kMaxK];
+    load_samples<PREC>(a.samples, a.K, smp);
+    run_queue<Model, PREC, SR>(a, smp, to_time<PREC>(a.t_end));
+}
+
+// Several groups (heterogeneous structures and parameter sweeps), one queue
+// per group, in one persistent launch.  Each warp drains the groups in order;
+// a warp whose lanes have all finished group g moves on to g + 1 without
+// waiting for other warps.  Group descriptors live in global memory.
+constexpr int kMaxGroups = 16;
+
+struct BatchArgs {
+    int n_groups;
+    int normalise;
+    int K;
+    double t_end;
+    const RunArgs *groups;             // device [n_groups]
+    int8_t family[kMaxGroups];         // 0 general, 1..5 compiled structures
+    double samples[kMaxK];
+};
+
+}  // namespace ssa
+
+#include "ssa_models.h"
+
+namespace ssa {
+
+template <int FAM, int PREC, int SR>
+__device__ __forceinline__ void run_family(const RunArgs &a, int normalise, const typename ModeTraits<PREC>::P *smp,
+                                           typename ModeTraits<PREC>::P t_end)
+{
+    if constexpr (FAM == 1) run_queue<StaticModel<models::BirthDeath, false>, PREC, SR>(a, smp, t_end);
+    else if constexpr (FAM == 2) {
+        if (normalise) run_queue<StaticModel<models::Schlogl, true>, PREC, SR>(a, smp, t_end);
+        else run_queue<StaticModel<models::Schlogl, false>, PREC, SR>(a, smp, t_end);
+    }
+    else if constexpr (FAM == 3) run_queue<StaticModel<models::Telegraph, false>, PREC, SR>(a, smp, t_end);
+    else if constexpr (FAM == 4) run_queue<StaticModel<models::Dimer, false>, PREC, SR>(a, smp, t_end);
+    else if constexpr (FAM == 5) run_queue<StaticModel<models::Repressilator, false>, PREC, SR>(a, smp, t_end);
+    else run_queue<GeneralModel, PREC, SR>(a, smp, t_end);
+}
+
+// FAMS lists the structure families compiled into this instantiation; a
+// group whose family is not listed is skipped (the host never sends one).
+template <int PREC, int SR, int... FAMS>
+__global__ void __launch_bounds__(256) ssa_batch_kernel(const __grid_constant__ BatchArgs b)
+{
+    using P = typename ModeTraits<PREC>::P;
+    __shared__ P smp[kMaxK];
+    load_samples<PREC>(b.samples, b.K, smp);
+    const P t_end = to_time<PREC>(b.t_end);
+    for (int g = 0; g < b.n_groups; ++g) {
+        const RunArgs &a = b.groups[g];
+        const int fam = b.family[g];
+        ((fam == FAMS ? (run_family<FAMS, PREC, SR>(a, b.normalise, smp, t_end), 0) : 0), ...);
     }
 }
 

@@ -11,6 +11,7 @@ namespace ssa {
 struct LaunchConfig {
     int block;          // threads per block (multiple of 32, <= 256)
     int blocks_per_sm;  // 0: as many as occupancy allows
+    int slice_pairs;    // step pairs between refill checks
 };
 
 // Launch the persistent kernel of one family for precision `prec`, rounding
@@ -52,11 +53,41 @@ cudaError_t launch_family(const RunArgs &a, int prec, int sr, LaunchConfig cfg, 
     if (per_sm < 1) per_sm = 1;
     if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;
     long long grid = (long long)sms * per_sm;
-    const long long need = (a.n_traj + cfg.block - 1) / cfg.block;
+    const long long need = (a.n_work + cfg.block - 1) / cfg.block;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     *grid_out = (int)grid;
     k<<<(unsigned)grid, (unsigned)cfg.block, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+// Batched launch over heterogeneous groups (ssa_k_batch_*.cu).  `work` is the
+// total number of items over all groups (caps the grid).  `compact` selects
+// the instantiation holding only the telegraph, dimer and repressilator
+// structures (fewer registers, higher occupancy) instead of every family.
+cudaError_t launch_batch(const BatchArgs &b, int64_t work, int prec, int sr, bool compact, LaunchConfig cfg,
+                         cudaStream_t stream, int *grid_out);
+
+template <int PREC, int SR>
+cudaError_t launch_batch_mode(const BatchArgs &b, int64_t work, bool compact, LaunchConfig cfg, cudaStream_t stream,
+                              int *grid_out)
+{
+    auto k = compact ? ssa_batch_kernel<PREC, SR, 3, 4, 5> : ssa_batch_kernel<PREC, SR, 1, 2, 3, 4, 5, 0>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, cfg.block, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;
+    long long grid = (long long)sms * per_sm;
+    const long long need = (work + cfg.block - 1) / cfg.block;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    *grid_out = (int)grid;
+    k<<<(unsigned)grid, (unsigned)cfg.block, 0, stream>>>(b);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,12 @@ SIGNATURES = {
     "ssa_model_kernel_family": (_I, [_P]),
     "ssa_ensemble_run": (_I, _RUN_ARGS),
     "ssa_ensemble_run_host": (_I, _RUN_ARGS),
-    "ssa_set_launch_config": (_I, [_I, _I]),
+    "ssa_set_launch_config": (_I, [_I, _I, _I]),
+    "ssa_batch_create": (_I, [_I, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, ctypes.POINTER(_P)]),
+    "ssa_batch_launch": (_I, [_P, _P]),
+    "ssa_batch_autotune": (_I, [_P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                ctypes.POINTER(_D)]),
+    "ssa_batch_destroy": (None, [_P]),
     "ssa_last_error": (ctypes.c_char_p, []),
 }
 
@@ -113,9 +118,9 @@ class Model:
             pass
 
 
-def set_launch_config(threads_per_block=128, blocks_per_sm=0):
+def set_launch_config(threads_per_block=128, blocks_per_sm=0, slice_pairs=1):
     """Launch shape for later runs (speed only; results do not depend on it)."""
-    _check(lib().ssa_set_launch_config(int(threads_per_block), int(blocks_per_sm)))
+    _check(lib().ssa_set_launch_config(int(threads_per_block), int(blocks_per_sm), int(slice_pairs)))
 
 
 def _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision, rounding, normalise, seed,
@@ -179,3 +184,78 @@ def ensemble_run_host(model, n_traj, x0, t_end, sample_times, precision="fp64", 
                                        int(max_events), int(state_bytes), _np_ptr(out), _np_ptr(status),
                                        _np_ptr(n_events), _np_ptr(t_final), sp))
     return {"snapshots": out, "status": status, "n_events": n_events, "t_final": t_final}
+
+
+class BatchGroup(ctypes.Structure):
+    """Mirror of ssa_batch_group in include/ssa.h."""
+    _fields_ = [("model", _P), ("n_sets", _I64), ("traj_per_set", _I64), ("rates", _P), ("hill", _P), ("x0", _P),
+                ("traj_offset", _U64), ("out", _P), ("traj_status", _P), ("n_events", _P), ("t_final", _P)]
+
+
+class Batch:
+    """ssa_batch_*: several groups (model + parameter sweep) in one persistent launch.
+
+    ``groups`` is a list of dicts with keys ``model`` (Model), ``x0`` [S, N],
+    ``traj_per_set``, optional ``rates`` [S, M], ``hill`` [S, M, 2],
+    ``traj_offset``.  Device outputs are allocated here (torch) and exposed as
+    ``self.outputs[g]``."""
+
+    def __init__(self, groups, t_end, sample_times, precision="mixed_f16", rounding="rn", normalise=False, seed=0,
+                 max_events=10**9, state_bytes=4):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        st = np.ascontiguousarray(np.atleast_1d(sample_times), dtype=np.float64)
+        K = st.size
+        self._keep = [st]
+        self.outputs = []
+        arr = (BatchGroup * len(groups))()
+        for g, G in enumerate(groups):
+            m = G["model"]
+            x0 = np.ascontiguousarray(G["x0"], dtype=np.int32).reshape(-1, m.N)
+            S = x0.shape[0]
+            T = int(G["traj_per_set"])
+            rates = G.get("rates")
+            rates = None if rates is None else np.ascontiguousarray(rates, dtype=np.float64).reshape(S, m.M)
+            hill = G.get("hill")
+            hill = None if hill is None else np.ascontiguousarray(hill, dtype=np.float64).reshape(S, m.M, 2)
+            n = S * T
+            o = {"snapshots": torch.empty((K, m.N, n), dtype=torch.int16 if state_bytes == 2 else torch.int32,
+                                          device=dev),
+                 "status": torch.empty(n, dtype=torch.int32, device=dev),
+                 "n_events": torch.empty(n, dtype=torch.int64, device=dev),
+                 "t_final": torch.empty(n, dtype=torch.float64, device=dev)}
+            self.outputs.append(o)
+            self._keep += [x0, rates, hill, m]
+            arr[g] = BatchGroup(m.handle, S, T, _np_ptr(rates), _np_ptr(hill), _np_ptr(x0), int(G.get("traj_offset", 0)),
+                                o["snapshots"].data_ptr(), o["status"].data_ptr(), o["n_events"].data_ptr(),
+                                o["t_final"].data_ptr())
+        prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        rnd = ROUNDING[rounding] if isinstance(rounding, str) else int(rounding)
+        h = _P()
+        _check(lib().ssa_batch_create(len(groups), ctypes.cast(arr, _P), float(t_end), K, _np_ptr(st), prec, rnd,
+                                      int(bool(normalise)), int(seed) & (2**64 - 1), int(max_events),
+                                      int(state_bytes), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        """Asynchronous; a torch stream replays a captured CUDA graph."""
+        sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        _check(lib().ssa_batch_launch(self._h, sp))
+
+    def autotune(self, stream=None):
+        sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        b, p, sl, ms = _I(), _I(), _I(), _D()
+        _check(lib().ssa_batch_autotune(self._h, sp, ctypes.byref(b), ctypes.byref(p), ctypes.byref(sl),
+                                        ctypes.byref(ms)))
+        return {"threads_per_block": b.value, "blocks_per_sm": p.value, "slice_pairs": sl.value, "ms": ms.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ssa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -108,7 +108,29 @@ def test_run_rejects_before_launch(ssa, case):
 
 def test_launch_config_validation(ssa):
     with pytest.raises(ssa.SSAError):
-        ssa.set_launch_config(48, 0)
+        ssa.set_launch_config(48, 0, 1)
     with pytest.raises(ssa.SSAError):
-        ssa.set_launch_config(512, 0)
-    ssa.set_launch_config(128, 0)
+        ssa.set_launch_config(512, 0, 1)
+    ssa.set_launch_config(128, 0, 1)
+
+
+def test_batch_create_rejects_before_allocating(ssa):
+    """Group validation happens on the host before any device allocation."""
+    m = ssa.Model.from_dict(P.telegraph())
+    x0 = np.ascontiguousarray(np.tile(P.TELEGRAPH_X0, (2, 1)), dtype=np.int32)
+    bad_rates = np.array([[0.1, 0.1, 5.0, 1.0], [0.1, -1.0, 5.0, 1.0]])
+    samples = np.array([10.0])
+    L = ssa.lib()
+    for rates, n_groups in [(bad_rates, 1), (None, 0), (None, 17)]:
+        arr = (ssa.BatchGroup * 1)()
+        arr[0] = ssa.BatchGroup(m.handle, 2, 4, ssa._np_ptr(rates), None, ssa._np_ptr(x0), 0, None, None, None, None)
+        h = ctypes.c_void_p()
+        rc = L.ssa_batch_create(n_groups, ctypes.cast(arr, ctypes.c_void_p), 10.0, 1, ssa._np_ptr(samples), 2, 0, 0,
+                                0, 1000, 4, ctypes.byref(h))
+        assert rc == ssa.SSA_EINVAL and not h.value
+    # outputs missing for a non-empty group
+    arr = (ssa.BatchGroup * 1)()
+    arr[0] = ssa.BatchGroup(m.handle, 2, 4, None, None, ssa._np_ptr(x0), 0, None, None, None, None)
+    h = ctypes.c_void_p()
+    assert L.ssa_batch_create(1, ctypes.cast(arr, ctypes.c_void_p), 10.0, 1, ssa._np_ptr(samples), 2, 0, 0, 0, 1000,
+                              4, ctypes.byref(h)) == ssa.SSA_EINVAL

@@ -29,6 +29,7 @@
 #ifndef SSA_H
 #define SSA_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -232,6 +233,51 @@ int ssa_batch_autotune(ssa_batch *batch, void *stream, int *threads_per_block, i
 /* Release the batch and its device memory (NULL is allowed).  No launch of
  * it may still be running. */
 void ssa_batch_destroy(ssa_batch *batch);
+
+/*
+ * ssa_sweep_run_noalloc -- a parameter sweep of one model that allocates no
+ * memory (the paper has no counterpart; this is a deployment entry point).
+ *
+ * For callers that cannot allocate device memory while they simulate:
+ * programs whose device memory belongs to another allocator or is held to a
+ * fixed budget after start-up, and real-time or embedded loops that forbid
+ * allocation on their hot path.  The call makes no cudaMalloc, cudaFree or
+ * other allocating call, on the device or the host; the caller passes the
+ * inputs and owns the outputs.  Its scratch (the work-queue counter and the
+ * per-set tables) lives in one static device array of
+ * SSA_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.
+ *
+ * Semantics equal n_sets calls of ssa_ensemble_run: trajectory r belongs to
+ * set r / traj_per_set, uses rates[set] (host [n_sets][M] c-convention, or
+ * NULL for the model's), hill[set] (host [n_sets][M][2] {alpha0, alpha}, or
+ * NULL) and x0[set] (host [n_sets][N]), and has global id traj_offset + r.
+ * Outputs: device [K][N][n_sets*traj_per_set], [n_sets*traj_per_set] ...
+ * as in ssa_ensemble_run.
+ *
+ *  - Sweeps needing more than SSA_NOALLOC_SCRATCH_BYTES of scratch
+ *    (ssa_sweep_noalloc_scratch_bytes) are rejected with SSA_EINVAL and a
+ *    message; split them into smaller sweeps.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) for that device; make that first call before any
+ *    stream capture.
+ *  - Every call shares the one array, which keeps the previous call's
+ *    contents (the call resets what must start at zero).  Calls whose work
+ *    overlaps on the GPU (other streams, other threads) race on it:
+ *    serialise them.
+ *  - Asynchronous on `stream`, except that the per-set tables are staged from
+ *    pageable host memory before the call returns.
+ */
+enum { SSA_NOALLOC_SCRATCH_BYTES = 1 << 20 };
+
+size_t ssa_sweep_noalloc_scratch_bytes(int n_species, int n_reactions, int64_t n_sets);
+
+int ssa_sweep_run_noalloc(const ssa_model *model, int64_t n_sets, int64_t traj_per_set,
+                          const double *rates, const double *hill, const int32_t *x0,
+                          uint64_t traj_offset, double t_end, int n_samples, const double *sample_times,
+                          int precision, int rounding, int normalise, uint64_t seed,
+                          int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
+                          int64_t *n_events, double *t_final, void *stream);
 
 /* Thread-local description of the last error on the calling thread. */
 const char *ssa_last_error(void);

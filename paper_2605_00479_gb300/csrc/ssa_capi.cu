@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -675,5 +676,173 @@ int ssa_batch_autotune(ssa_batch *b, void *stream, int *threads_per_block, int *
 }
 
 void ssa_batch_destroy(ssa_batch *b) { batch_free(b); }
+
+}  // extern "C"
+
+// ======================================================================
+// Parameter sweep without allocation
+// ======================================================================
+// Some callers cannot allocate device memory when they run a simulation:
+// programs whose device memory is owned by another allocator or held to a
+// fixed budget after start-up, and real-time or embedded loops that forbid
+// allocation on their hot path.  For them the sweep's scratch memory (the
+// work-queue counter and the per-set rate and initial-state tables) lives in
+// one static device array that every GPU loading this library keeps until
+// the process exits.  In host code `g_noalloc_scratch` names a host-side
+// stand-in, never a device address: the device address is looked up once
+// per device with cudaGetSymbolAddress and then passed to the kernel.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SSA_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices];   // device address of the scratch per device ordinal
+
+int noalloc_scratch(void **ptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(SSA_EINVAL, "device ordinal %d beyond %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return SSA_OK;
+}
+
+// Copy host values to the device through a fixed stack buffer (no heap).
+template <class T, class F>
+cudaError_t upload_chunked(T *dst, size_t count, F value, cudaStream_t s)
+{
+    T buf[512];
+    for (size_t at = 0; at < count;) {
+        const size_t n = count - at < 512 ? count - at : 512;
+        for (size_t q = 0; q < n; ++q) buf[q] = value(at + q);
+        // pageable source: the call returns once `buf` has been staged
+        const cudaError_t e = cudaMemcpyAsync(dst + at, buf, sizeof(T) * n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        at += n;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ssa_sweep_noalloc_scratch_bytes(int n_species, int n_reactions, int64_t n_sets)
+{
+    if (n_sets < 0) return 0;
+    const GroupTables T = group_tables(n_sets, n_reactions, n_species);
+    return 256 + T.total();
+}
+
+int ssa_sweep_run_noalloc(const ssa_model *model, int64_t n_sets, int64_t traj_per_set, const double *rates,
+                          const double *hill, const int32_t *x0, uint64_t traj_offset, double t_end, int n_samples,
+                          const double *sample_times, int precision, int rounding, int normalise, uint64_t seed,
+                          int64_t max_events, int state_bytes, void *out, uint32_t *traj_status, int64_t *n_events,
+                          double *t_final, void *stream)
+{
+    if (!model) return fail(SSA_EINVAL, "model is NULL");
+    if (n_sets < 1 || traj_per_set < 0) return fail(SSA_EINVAL, "n_sets >= 1 and traj_per_set >= 0");
+    if (!x0) return fail(SSA_EINVAL, "x0 is NULL");
+    const ssa_model &m = *model;
+    const size_t need = ssa_sweep_noalloc_scratch_bytes(m.N, m.M, n_sets);
+    if (need > (size_t)SSA_NOALLOC_SCRATCH_BYTES)
+        return fail(SSA_EINVAL, "sweep needs %zu bytes of scratch, the static scratch holds %d: split it into sweeps "
+                                "of fewer parameter sets", need, SSA_NOALLOC_SCRATCH_BYTES);
+    const int64_t items = n_sets * traj_per_set;
+    for (int64_t q = 0; q < n_sets; ++q) {
+        const int rc = validate_run(model, items, traj_offset, x0 + q * m.N, t_end, n_samples, sample_times, precision,
+                                    rounding, max_events, state_bytes);
+        if (rc != SSA_OK) return rc;
+        for (int j = 0; j < m.M; ++j) {
+            if (rates && m.law[j] == SSA_LAW_MASS_ACTION && (!finite_double(rates[q * m.M + j]) || rates[q * m.M + j] < 0.0))
+                return fail(SSA_EINVAL, "set %lld: rate %d must be finite and >= 0", (long long)q, j);
+            if (hill && m.law[j] == SSA_LAW_HILL_REPRESSION)
+                for (int c = 0; c < 2; ++c) {
+                    const double v = hill[(q * m.M + j) * 2 + c];
+                    if (!finite_double(v) || v < 0.0)
+                        return fail(SSA_EINVAL, "set %lld: Hill amplitudes must be finite and >= 0", (long long)q);
+                }
+        }
+    }
+    if (items > 0 && (!out || !traj_status)) return fail(SSA_EINVAL, "out and traj_status are required");
+    if (items == 0) return SSA_OK;
+
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != SSA_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long *head = static_cast<unsigned long long *>(scratch);
+    const GroupTables T = group_tables(n_sets, m.M, m.N);
+    double *d_cp = reinterpret_cast<double *>(static_cast<char *>(scratch) + 256);
+    double *d_hl = reinterpret_cast<double *>(reinterpret_cast<char *>(d_cp) + T.cprime);
+    int32_t *d_x0 = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(d_hl) + T.hill);
+
+    // per-set c' in binary64 (same folding as every other entry point)
+    auto cprime_of = [&](size_t idx) {
+        const int64_t q = (int64_t)(idx / (size_t)m.M);
+        ssa_model mq = m;
+        if (rates)
+            for (int j = 0; j < m.M; ++j) mq.rate[j] = rates[q * m.M + j];
+        double c[ssa::kMaxM];
+        int8_t folded[ssa::kMaxM][ssa::kMaxN];
+        rate_constants(mq, x0 + q * m.N, normalise, c, folded);
+        return c[idx % (size_t)m.M];
+    };
+    auto hill_of = [&](size_t idx) {
+        const size_t jq = idx / 2;
+        const int64_t q = (int64_t)(jq / (size_t)m.M);
+        const int j = (int)(jq % (size_t)m.M);
+        if (m.law[j] != SSA_LAW_HILL_REPRESSION) return 0.0;
+        return hill ? hill[(q * m.M + j) * 2 + (idx & 1)] : m.hill[j][idx & 1];
+    };
+    ssa::RunArgs a;   // on the stack: no heap allocation either
+    std::memset(&a, 0, sizeof(a));
+    fill_structure(m, normalise, x0, a);
+    for (int j = 0; j < m.M; ++j) {
+        a.cprime[j] = cprime_of((size_t)j);
+        a.hill_a0[j] = hill_of((size_t)j * 2);
+        a.hill_a[j] = hill_of((size_t)j * 2 + 1);
+    }
+    a.K = n_samples;
+    a.n_traj = items;
+    a.n_work = items;
+    a.slice_pairs = g_cfg.slice_pairs;
+    a.traj_offset = (uint32_t)traj_offset;
+    a.n_sets = (int)n_sets;
+    a.traj_per_set = traj_per_set > 0 ? traj_per_set : 1;
+    a.cprime_tab = d_cp;
+    a.hill_tab = d_hl;
+    a.x0_tab = d_x0;
+    a.t_end = t_end;
+    for (int k = 0; k < n_samples; ++k) a.samples[k] = sample_times[k];
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.max_events = max_events;
+    a.out = out;
+    a.state_bytes = state_bytes;
+    a.status = traj_status;
+    a.n_events = n_events;
+    a.t_final = t_final;
+    a.queue_head = head;
+
+    // the scratch keeps the previous call's contents: reset the queue counter
+    cudaError_t e = cudaMemsetAsync(head, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = upload_chunked(d_cp, (size_t)n_sets * m.M, cprime_of, s);
+    if (e == cudaSuccess) e = upload_chunked(d_hl, (size_t)n_sets * m.M * 2, hill_of, s);
+    if (e == cudaSuccess) e = upload_chunked(d_x0, (size_t)n_sets * m.N, [&](size_t i) { return x0[i]; }, s);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch upload");
+    int grid = 0;
+    e = launcher_for(m.family)(a, precision, rounding, normalise ? 1 : 0, g_cfg, s, &grid);
+    return e == cudaSuccess ? SSA_OK : cuda_fail(e, "kernel launch");
+}
 
 }  // extern "C"

@@ -37,6 +37,9 @@ SIGNATURES = {
     "ssa_batch_autotune": (_I, [_P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                 ctypes.POINTER(_D)]),
     "ssa_batch_destroy": (None, [_P]),
+    "ssa_sweep_noalloc_scratch_bytes": (ctypes.c_size_t, [_I, _I, _I64]),
+    "ssa_sweep_run_noalloc": (_I, [_P, _I64, _I64, _P, _P, _P, _U64, _D, _I, _P, _I, _I, _I, _U64, _I64, _I,
+                                   _P, _P, _P, _P, _P]),
     "ssa_last_error": (ctypes.c_char_p, []),
 }
 

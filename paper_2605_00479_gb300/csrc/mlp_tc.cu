@@ -1,0 +1,353 @@
+// mlp_tc.cu -- tcgen05 GEMM with fused epilogues, pack kernels, and the GEMM
+// test entry of the C ABI.  See mlp_tc.cuh for the operand layout.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "../../include/ssa.h"
+#include "mlp_tc.cuh"
+
+namespace mlp {
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading byte
+// offset (between core matrices along K), stride byte offset (between 8-row
+// groups along M/N), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+// 32 lanes x 16 consecutive fp32 columns: thread t of the warp gets its row.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint16_t f2bf(float x)
+{
+    uint16_t h;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(x));
+    return h;
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+    const float pdf = 0.39894228040143268f * expf(-0.5f * z * z);
+    return cdf + z * pdf;
+}
+
+// 16 bf16 values of row r, columns c0..c0+15 into a packed matrix with C columns
+__device__ __forceinline__ void store_packed16(uint8_t *base, int64_t r, int c0, int C, const uint16_t (&h)[16])
+{
+    uint4 lo, hi;
+    lo.x = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+    lo.y = (uint32_t)h[2] | ((uint32_t)h[3] << 16);
+    lo.z = (uint32_t)h[4] | ((uint32_t)h[5] << 16);
+    lo.w = (uint32_t)h[6] | ((uint32_t)h[7] << 16);
+    hi.x = (uint32_t)h[8] | ((uint32_t)h[9] << 16);
+    hi.y = (uint32_t)h[10] | ((uint32_t)h[11] << 16);
+    hi.z = (uint32_t)h[12] | ((uint32_t)h[13] << 16);
+    hi.w = (uint32_t)h[14] | ((uint32_t)h[15] << 16);
+    *reinterpret_cast<uint4 *>(base + packed_offset(r, c0, C)) = lo;
+    *reinterpret_cast<uint4 *>(base + packed_offset(r, c0 + 8, C)) = hi;
+}
+
+// ------------------------------------------------------------ the GEMM
+__global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ GemmArgs g)
+{
+    extern __shared__ uint8_t dyn_smem[];
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t tmem_base_s;
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_smem) + 127) & ~uintptr_t(127));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + (size_t)kTileM * g.kchunk * 2;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x;
+    const uint32_t ncols = g.N <= 32 ? 32u : (g.N <= 64 ? 64u : (g.N <= 128 ? 128u : 256u));
+    if (warp == 0) tmem_alloc(&tmem_base_s, ncols);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_d = tmem_base_s;
+
+    const int n_chunks = g.K / g.kchunk;
+    const uint32_t idesc = instr_desc_bf16_f32(kTileM, g.N);
+    const uint32_t rg_bytes = (uint32_t)g.kchunk * 16u;   // one 8-row group of one stage
+    const uint32_t stage_bytes = (uint32_t)(kTileM + g.N) * (uint32_t)g.kchunk * 2u;
+    int err = ERR_NONE;
+    int ch = 0;
+    for (; ch < n_chunks; ++ch) {
+        const uint32_t parity = (uint32_t)(ch & 1);
+        if (warp == 0) {
+            if (lane == 0) mbar_expect_tx(&bars[0], stage_bytes);
+            __syncwarp();
+            const int colA = g.a_col0 + ch * g.kchunk, colB = g.b_col0 + ch * g.kchunk;
+            const int groups = kTileM / 8 + g.N / 8;
+            for (int q = lane; q < groups; q += 32) {
+                if (q < kTileM / 8) {
+                    const int64_t rg = (int64_t)tile * (kTileM / 8) + q;
+                    bulk_g2s(sA + (size_t)q * rg_bytes, g.A + (rg * (g.lda_cols / 8) + colA / 8) * 128, rg_bytes, &bars[0]);
+                } else {
+                    const int64_t rg = q - kTileM / 8;
+                    bulk_g2s(sB + (size_t)rg * rg_bytes, g.B + (rg * (g.ldb_cols / 8) + colB / 8) * 128, rg_bytes,
+                             &bars[0]);
+                }
+            }
+        }
+        if (!mbar_wait(&bars[0], parity)) {
+            err = ERR_LOAD_TIMEOUT;
+            break;
+        }
+        tc_fence_after();
+        if (tid == 0) {
+            const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+            for (int s = 0; s < g.kchunk / 16; ++s) {
+                const uint64_t ad = smem_desc(a0 + (uint32_t)s * 256u, 128u, rg_bytes);
+                const uint64_t bd = smem_desc(b0 + (uint32_t)s * 256u, 128u, rg_bytes);
+                mma_bf16(tmem_d, ad, bd, idesc, (ch > 0 || s > 0) ? 1u : 0u);
+            }
+            mma_commit(&bars[1]);
+        }
+        __syncwarp();
+        if (!mbar_wait(&bars[1], parity)) {
+            err = ERR_MMA_TIMEOUT;
+            break;
+        }
+    }
+    const bool ok = __syncthreads_and(err == ERR_NONE) != 0;
+    tc_fence_after();
+
+    if (ok) {
+        const int64_t row = (int64_t)tile * kTileM + warp * 32 + lane;
+        const bool valid = row < g.M;
+        for (int c0 = 0; c0 < g.N; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (g.epi == EPI_STORE_F32 || g.epi == EPI_LOGITS) {
+                if (valid) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        g.fout[row * g.ld_fout + c0 + i] = v[i] + (g.epi == EPI_LOGITS ? g.bias[c0 + i] : 0.0f);
+                }
+            } else {
+                uint16_t h[16];
+                float dz[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    float y;
+                    if (g.epi == EPI_HIDDEN_FWD) {
+                        const float z = v[i] + g.bias[c0 + i];
+                        if (valid) g.fout[row * g.ld_fout + c0 + i] = z;
+                        y = gelu(z);
+                    } else {
+                        y = valid ? v[i] * gelu_grad(g.zin[row * g.N + c0 + i]) : 0.0f;
+                    }
+                    if (!valid) y = 0.0f;
+                    dz[i] = y;
+                    h[i] = f2bf(y);
+                }
+                store_packed16(g.pk_out, row, c0, g.N, h);
+                if (g.pkT_out) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        *reinterpret_cast<uint16_t *>(g.pkT_out + packed_offset(c0 + i, row, g.pkT_cols)) = h[i];
+                }
+                if (g.epi == EPI_HIDDEN_BWD && g.bias_grad) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        float s = dz[i];
+                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+                        if (lane == 0) atomicAdd(&g.bias_grad[c0 + i], s);
+                    }
+                }
+            }
+        }
+    } else {
+        if (tid == 0) atomicExch(g.error, err);
+        // let our own copies and MMAs drain (bounded) before tensor memory is freed
+        mbar_wait(&bars[0], (uint32_t)(ch & 1));
+        mbar_wait(&bars[1], (uint32_t)(ch & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem_d, ncols);
+}
+
+// ------------------------------------------------------------ packing
+// Row-major bf16 [rows][cols] (leading dimension ld) -> packed [rows_pad][C].
+// One thread per 16-byte core-matrix row; padding is zero.
+__global__ void pack_bf16_kernel(const uint16_t *src, int rows, int cols, int ld, uint8_t *dst, int rows_pad, int C)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per_row = C / 8;
+    if (idx >= (int64_t)rows_pad * per_row) return;
+    const int64_t r = idx / per_row;
+    const int c0 = (int)(idx % per_row) * 8;
+    uint16_t h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = (r < rows && c0 + i < cols) ? src[r * ld + c0 + i] : (uint16_t)0;
+    uint4 v;
+    v.x = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+    v.y = (uint32_t)h[2] | ((uint32_t)h[3] << 16);
+    v.z = (uint32_t)h[4] | ((uint32_t)h[5] << 16);
+    v.w = (uint32_t)h[6] | ((uint32_t)h[7] << 16);
+    *reinterpret_cast<uint4 *>(dst + packed_offset(r, c0, C)) = v;
+}
+
+cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s)
+{
+    // Shared memory also caps how many CTAs share an SM: request enough that
+    // their tensor-memory columns (ncols each) never exceed the SM's 512.
+    const int ncols = g.N <= 32 ? 32 : (g.N <= 64 ? 64 : (g.N <= 128 ? 128 : 256));
+    const size_t per_sm = 233472, reserve = 1024;
+    const size_t cap_ctas = (size_t)(512 / ncols);
+    size_t smem = (size_t)(kTileM + g.N) * (size_t)g.kchunk * 2 + 128;
+    const size_t floor_bytes = per_sm / (cap_ctas + 1) + 1 - reserve;
+    if (smem < floor_bytes) smem = floor_bytes;
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = (g.M + kTileM - 1) / kTileM;
+    gemm_kernel<<<tiles, 128, smem, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const uint16_t *src, int rows, int cols, int ld, uint8_t *dst, int rows_pad, int C,
+                        cudaStream_t s)
+{
+    const int64_t n = (int64_t)rows_pad * (C / 8);
+    pack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, rows, cols, ld, dst, rows_pad, C);
+    return cudaGetLastError();
+}
+
+}  // namespace mlp
+
+// ------------------------------------------------------------ C ABI test entry
+extern "C" int ssa_mlp_gemm_bf16(int M, int N, int K, const uint16_t *A, const uint16_t *B, float *D, void *stream)
+{
+    if (M < 1 || N < 16 || N > mlp::kMaxN || N % 16 != 0 || K < 16 || K % 16 != 0 || (K > 256 && K % 256 != 0) ||
+        !A || !B || !D)
+        return SSA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int Mpad = (M + mlp::kTileM - 1) / mlp::kTileM * mlp::kTileM;
+    const size_t a_bytes = (size_t)Mpad * K * 2, b_bytes = (size_t)N * K * 2;
+    uint8_t *buf = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&buf), a_bytes + b_bytes + 256, s) != cudaSuccess) return SSA_ENOMEM;
+    int *err = reinterpret_cast<int *>(buf + a_bytes + b_bytes);
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = mlp::launch_pack(A, M, K, K, buf, Mpad, K, s);
+    if (e == cudaSuccess) e = mlp::launch_pack(B, N, K, K, buf + a_bytes, N, K, s);
+    mlp::GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = buf;
+    g.B = buf + a_bytes;
+    g.lda_cols = K;
+    g.ldb_cols = K;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.kchunk = K > 256 ? 256 : K;
+    g.epi = mlp::EPI_STORE_F32;
+    g.fout = D;
+    g.ld_fout = N;
+    g.error = err;
+    if (e == cudaSuccess) e = mlp::launch_gemm(g, s);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) return SSA_ECUDA;
+    return herr ? SSA_ETIMEDOUT : SSA_OK;
+}

@@ -40,6 +40,7 @@ SIGNATURES = {
     "ssa_sweep_noalloc_scratch_bytes": (ctypes.c_size_t, [_I, _I, _I64]),
     "ssa_sweep_run_noalloc": (_I, [_P, _I64, _I64, _P, _P, _P, _U64, _D, _I, _P, _I, _I, _I, _U64, _I64, _I,
                                    _P, _P, _P, _P, _P]),
+    "ssa_mlp_gemm_bf16": (_I, [_I, _I, _I, _P, _P, _P, _P]),
     "ssa_last_error": (ctypes.c_char_p, []),
 }
 

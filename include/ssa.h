@@ -279,6 +279,68 @@ int ssa_sweep_run_noalloc(const ssa_model *model, int64_t n_sets, int64_t traj_p
                           int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
                           int64_t *n_events, double *t_final, void *stream);
 
+/*
+ * Learned surrogate for the telegraph model (a spec extension; the
+ * paper trains no network).  A multilayer perceptron maps 4 standardised
+ * log-parameters (log kon, log koff, log km, log gamma) through three hidden
+ * layers of 256 GELU units to a 128-bin softmax over the mRNA count (bins
+ * 0..127, the last holding >= 127).  bf16 weights and activations, fp32
+ * accumulation in tensor memory (tcgen05), fp32 master weights with AdamW,
+ * cross-entropy against SSA histograms.  Parameter vector (fp32, host or
+ * device as stated): W1 [256][16] (input columns 4..15 are padding, kept 0),
+ * b1 [256], W2 [256][256], b2 [256], W3 [256][256], b3 [256], W4 [128][256],
+ * b4 [128]; ssa_surrogate_param_count() values.
+ */
+typedef struct ssa_surrogate ssa_surrogate;
+
+int64_t ssa_surrogate_param_count(void);
+
+/* Allocate weights, optimiser state and activations for batches of up to
+ * max_batch rows (1..2^20); He-normal initialisation from `seed`.
+ * Synchronous.  Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA. */
+int ssa_surrogate_create(int max_batch, uint64_t seed, ssa_surrogate **out);
+void ssa_surrogate_destroy(ssa_surrogate *s);
+
+/* Replace / read the fp32 parameter vector (host [param_count]); setting
+ * resets the optimiser state.  Synchronous. */
+int ssa_surrogate_set_params(ssa_surrogate *s, const float *params);
+int ssa_surrogate_get_params(ssa_surrogate *s, float *params);
+
+/* probs (device [B][128]) = softmax(network(features)), features device
+ * [B][4].  Asynchronous on stream. */
+int ssa_surrogate_predict(ssa_surrogate *s, int B, const float *features, float *probs, void *stream);
+
+/* One AdamW step (beta = 0.9, 0.999; eps = 1e-8; decoupled weight decay on
+ * the weights) on the mean cross-entropy of the batch against targets
+ * (device [B][128], rows summing to 1).  loss_out: device float or NULL.
+ * Asynchronous on stream. */
+int ssa_surrogate_train_step(ssa_surrogate *s, int B, const float *features, const float *targets, float lr,
+                             float weight_decay, float *loss_out, void *stream);
+
+/* Gradient of the mean cross-entropy (host [param_count]) and the loss
+ * (host float or NULL) without updating anything.  Synchronous. */
+int ssa_surrogate_gradients(ssa_surrogate *s, int B, const float *features, const float *targets,
+                            float *grads, float *loss);
+
+/* Synchronise and report a tensor-core pipeline timeout (SSA_ETIMEDOUT) if a
+ * GEMM's bounded wait gave up since creation. */
+int ssa_surrogate_status(ssa_surrogate *s);
+
+/* hist (device [n_sets][bins]) = normalised histogram of counts (device
+ * [n_sets * traj_per_set], set-major), counts clamped to [0, bins-1]. */
+int ssa_histogram(const int32_t *counts, int64_t n_sets, int64_t traj_per_set, int bins, float *hist,
+                  void *stream);
+
+/* w1 (device [rows]) = sum_b |CDF_p(b) - CDF_q(b)| for histograms p, q
+ * (device [rows][bins]): the Wasserstein-1 distance on the integers. */
+int ssa_hist_w1(const float *p, const float *q, int64_t rows, int bins, float *w1, void *stream);
+
+/* Tensor-core GEMM check: D (device [M][N] fp32) = A (device [M][K] bf16,
+ * row-major) times B (device [N][K] bf16, row-major) transposed.
+ * N in 16..256 and a multiple of 16; K a multiple of 16 (of 256 above 256).
+ * Synchronous; SSA_ETIMEDOUT if a bounded wait gave up. */
+int ssa_mlp_gemm_bf16(int M, int N, int K, const uint16_t *A, const uint16_t *B, float *D, void *stream);
+
 /* Thread-local description of the last error on the calling thread. */
 const char *ssa_last_error(void);
 

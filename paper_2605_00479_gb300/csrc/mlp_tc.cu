@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
 
     if (ok) {
         const int64_t row = (int64_t)tile * kTileM + warp * 32 + lane;
-        const bool valid = row < g.M;
+        const bool valid = row < g.m_valid;
         for (int c0 = 0; c0 < g.N; c0 += 16) {
             float v[16];
             tmem_ld16(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
@@ -336,6 +336,7 @@ extern "C" int ssa_mlp_gemm_bf16(int M, int N, int K, const uint16_t *A, const u
     g.lda_cols = K;
     g.ldb_cols = K;
     g.M = M;
+    g.m_valid = M;
     g.N = N;
     g.K = K;
     g.kchunk = K > 256 ? 256 : K;

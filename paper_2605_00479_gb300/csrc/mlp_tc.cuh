@@ -17,6 +17,8 @@
 // frees its tensor memory and returns.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace mlp {
@@ -40,7 +42,8 @@ struct GemmArgs {
     const uint8_t *B;          // packed, rows = N, C = ldb_cols
     int lda_cols, ldb_cols;    // C of the packed A / B matrices
     int a_col0, b_col0;        // first reduction column used (multiple of 16)
-    int M, N, K, kchunk;       // valid rows of D, columns, reduction length, columns per stage
+    int M, N, K, kchunk;       // rows of D computed (tiles of 128), columns, reduction length, columns per stage
+    int m_valid;               // rows < m_valid are real; the others are written as zeros (or skipped)
     int epi;
     const float *bias;         // [N]
     const float *zin;          // [M][N] pre-activations (EPI_HIDDEN_BWD)
@@ -66,5 +69,9 @@ __host__ __device__ inline int64_t packed_offset(int64_t r, int64_t c, int64_t C
 {
     return ((r >> 3) * (C >> 3) + (c >> 3)) * 128 + (r & 7) * 16 + (c & 7) * 2;
 }
+
+cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s);
+cudaError_t launch_pack(const uint16_t *src, int rows, int cols, int ld, uint8_t *dst, int rows_pad, int C,
+                        cudaStream_t s);
 
 }  // namespace mlp

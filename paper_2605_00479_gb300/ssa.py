@@ -41,6 +41,17 @@ SIGNATURES = {
     "ssa_sweep_run_noalloc": (_I, [_P, _I64, _I64, _P, _P, _P, _U64, _D, _I, _P, _I, _I, _I, _U64, _I64, _I,
                                    _P, _P, _P, _P, _P]),
     "ssa_mlp_gemm_bf16": (_I, [_I, _I, _I, _P, _P, _P, _P]),
+    "ssa_surrogate_param_count": (_I64, []),
+    "ssa_surrogate_create": (_I, [_I, _U64, ctypes.POINTER(_P)]),
+    "ssa_surrogate_destroy": (None, [_P]),
+    "ssa_surrogate_set_params": (_I, [_P, _P]),
+    "ssa_surrogate_get_params": (_I, [_P, _P]),
+    "ssa_surrogate_predict": (_I, [_P, _I, _P, _P, _P]),
+    "ssa_surrogate_train_step": (_I, [_P, _I, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P]),
+    "ssa_surrogate_gradients": (_I, [_P, _I, _P, _P, _P, _P]),
+    "ssa_surrogate_status": (_I, [_P]),
+    "ssa_histogram": (_I, [_P, _I64, _I64, _I, _P, _P]),
+    "ssa_hist_w1": (_I, [_P, _P, _I64, _I, _P, _P]),
     "ssa_last_error": (ctypes.c_char_p, []),
 }
 
@@ -263,3 +274,82 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Surrogate:
+    """ssa_surrogate_*: the telegraph surrogate network (marshalling only)."""
+
+    def __init__(self, max_batch, seed=0):
+        h = _P()
+        _check(lib().ssa_surrogate_create(int(max_batch), int(seed) & (2**64 - 1), ctypes.byref(h)))
+        self._h = h
+        self.n_params = int(lib().ssa_surrogate_param_count())
+
+    def get_params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().ssa_surrogate_get_params(self._h, _np_ptr(out)))
+        return out
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        assert theta.size == self.n_params
+        _check(lib().ssa_surrogate_set_params(self._h, _np_ptr(theta)))
+
+    def predict(self, features, probs=None, stream=None):
+        import torch
+        B = features.shape[0]
+        if probs is None:
+            probs = torch.empty((B, 128), dtype=torch.float32, device=features.device)
+        _check(lib().ssa_surrogate_predict(self._h, B, _dev_ptr(features), _dev_ptr(probs), _stream_ptr(stream)))
+        return probs
+
+    def train_step(self, features, targets, lr, weight_decay=1e-4, loss=None, stream=None):
+        _check(lib().ssa_surrogate_train_step(self._h, features.shape[0], _dev_ptr(features), _dev_ptr(targets),
+                                              float(lr), float(weight_decay), _dev_ptr(loss), _stream_ptr(stream)))
+
+    def gradients(self, features, targets):
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        _check(lib().ssa_surrogate_gradients(self._h, features.shape[0], _dev_ptr(features), _dev_ptr(targets),
+                                             _np_ptr(g), _np_ptr(loss)))
+        return float(loss[0]), g
+
+    def status(self):
+        _check(lib().ssa_surrogate_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ssa_surrogate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def histogram(counts, n_sets, traj_per_set, bins=128, hist=None, stream=None):
+    """Normalised per-set histograms (device) of device int32 counts."""
+    import torch
+    if hist is None:
+        hist = torch.empty((n_sets, bins), dtype=torch.float32, device=counts.device)
+    _check(lib().ssa_histogram(_dev_ptr(counts), int(n_sets), int(traj_per_set), int(bins), _dev_ptr(hist),
+                               _stream_ptr(stream)))
+    return hist
+
+
+def hist_w1(p, q, out=None, stream=None):
+    """Row-wise Wasserstein-1 distance between device histograms."""
+    import torch
+    rows, bins = p.shape
+    if out is None:
+        out = torch.empty(rows, dtype=torch.float32, device=p.device)
+    _check(lib().ssa_hist_w1(_dev_ptr(p), _dev_ptr(q), int(rows), int(bins), _dev_ptr(out), _stream_ptr(stream)))
+    return out

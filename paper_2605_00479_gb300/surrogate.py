@@ -1,0 +1,160 @@
+"""Learned surrogate for the telegraph model, trained on the SSA engine's output.
+
+Workflow (host orchestration of the CUDA kernels in libssa_gb300.so):
+  1. Training data: parameter sets (kon, koff log-uniform in [0.05, 5], km in
+     [5, 100], gamma in [0.5, 2]); for each, an ensemble of telegraph
+     trajectories to t_end = 200 in mixed binary16 precision, run as one
+     persistent batched launch; per-set histograms of the mRNA count over
+     bins 0..127 (the last holding >= 127).
+  2. Training: the 4 -> 256 -> 256 -> 256 -> 128 GELU network on the tensor
+     cores (tcgen05 GEMMs, bf16 operands, fp32 accumulation), AdamW with a
+     cosine learning-rate schedule, cross-entropy against the histograms.
+  3. Serving: predictions for query points; the SSA is the judge: each query
+     point's prediction is compared with a fresh SSA ensemble (Wasserstein-1
+     in copies) and points above the threshold (0.5 copies) are answered by
+     re-simulation instead.
+
+``python -m paper_2605_00479_gb300.surrogate`` runs the full configuration
+(2^16 training sets x 1024 trajectories, 2^14 query points) and prints one
+JSON line.
+"""
+from __future__ import annotations
+
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+from . import presets as P
+from . import ssa
+
+BINS = 128
+T_END = 200.0
+LOG_LO = np.log(np.array([0.05, 0.05, 5.0, 0.5]))
+LOG_HI = np.log(np.array([5.0, 5.0, 100.0, 2.0]))
+W1_THRESHOLD = 0.5
+
+
+def draw_parameters(n, seed):
+    """[n, 4] rate tables (kon, koff, km, gamma) for the telegraph model."""
+    return P.telegraph_sweep(n, seed=seed, gamma_range=(0.5, 2.0))
+
+
+def standardise(params):
+    """Log-parameters mapped affinely to [-1, 1] (network inputs)."""
+    return (2.0 * (np.log(params) - LOG_LO) / (LOG_HI - LOG_LO) - 1.0).astype(np.float32)
+
+
+def simulate_histograms(params, traj_per_set, seed, traj_offset=0, precision="mixed_f16", rounding="rn",
+                        chunk_sets=8192, stream=None):
+    """Per-set mRNA histograms [n_sets, 128] (device) from SSA ensembles."""
+    import torch
+    model = ssa.Model.from_dict(P.telegraph())
+    n = params.shape[0]
+    out = torch.empty((n, BINS), dtype=torch.float32, device="cuda")
+    for a in range(0, n, chunk_sets):
+        b = min(n, a + chunk_sets)
+        S = b - a
+        group = {"model": model, "x0": np.tile(P.TELEGRAPH_X0, (S, 1)), "rates": params[a:b],
+                 "traj_per_set": traj_per_set, "traj_offset": traj_offset + a * traj_per_set}
+        batch = ssa.Batch([group], T_END, [T_END], precision, rounding, seed=seed, max_events=10**7)
+        batch.launch(stream)
+        counts = batch.outputs[0]["snapshots"][0, 2]
+        ssa.histogram(counts, S, traj_per_set, BINS, hist=out[a:b], stream=stream)
+        batch.close()
+    return out
+
+
+def train(net, feats, hists, steps, batch_size, lr_max=2e-3, lr_min=5e-5, weight_decay=1e-4, seed=0):
+    """AdamW with a cosine schedule over random minibatches; returns the loss trace."""
+    import torch
+    n = feats.shape[0]
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    loss = torch.zeros(1, device="cuda")
+    trace = []
+    for step in range(steps):
+        idx = torch.randint(0, n, (batch_size,), device="cuda", generator=g)
+        lr = lr_min + 0.5 * (lr_max - lr_min) * (1 + math.cos(math.pi * step / max(1, steps - 1)))
+        net.train_step(feats[idx], hists[idx], lr, weight_decay, loss=loss)
+        if step % max(1, steps // 50) == 0 or step == steps - 1:
+            trace.append((step, float(loss)))
+    return trace
+
+
+def serve(net, query_params, judge_hist):
+    """Predict, judge against an SSA ensemble, fall back where W1 > threshold.
+
+    Returns (answer histograms, per-point W1 of the prediction, fallback mask)."""
+    import torch
+    feats = torch.from_numpy(standardise(query_params)).cuda()
+    q = net.predict(feats)
+    w1 = ssa.hist_w1(q, judge_hist)
+    fallback = w1 > W1_THRESHOLD
+    answer = torch.where(fallback[:, None], judge_hist, q)
+    return answer, w1, fallback
+
+
+def run(n_train=2**16, traj_train=1024, n_query=2**14, traj_query=1024, steps=6000, batch_size=1024, seed=2605):
+    """The full surrogate configuration; returns a report dict."""
+    import torch
+    torch.cuda.synchronize()
+    report = {"n_train_sets": n_train, "traj_per_set": traj_train, "n_query": n_query, "t_end": T_END,
+              "bins": BINS, "precision": "mixed_f16:rn", "w1_threshold": W1_THRESHOLD}
+    # 1. training data
+    tr = draw_parameters(n_train, seed)
+    t0 = time.perf_counter()
+    h_train = simulate_histograms(tr, traj_train, seed=seed, traj_offset=0)
+    torch.cuda.synchronize()
+    report["data_gen_s"] = time.perf_counter() - t0
+    f_train = torch.from_numpy(standardise(tr)).cuda()
+    # 2. training
+    net = ssa.Surrogate(max_batch=max(batch_size, n_query), seed=seed)
+    t0 = time.perf_counter()
+    trace = train(net, f_train, h_train, steps, batch_size, seed=seed)
+    torch.cuda.synchronize()
+    net.status()
+    report["train_s"] = time.perf_counter() - t0
+    report["train_steps"] = steps
+    report["loss_first"], report["loss_last"] = trace[0][1], trace[-1][1]
+    ent = -(h_train * torch.log(h_train.clamp_min(1e-30))).sum(dim=1).mean()
+    report["target_entropy"] = float(ent)
+    # 3. serving on held-out points against fresh SSA ensembles
+    qp = draw_parameters(n_query, seed + 1)
+    t0 = time.perf_counter()
+    judge = simulate_histograms(qp, traj_query, seed=seed + 7, traj_offset=2**31)
+    torch.cuda.synchronize()
+    ssa_s = time.perf_counter() - t0
+    twin = simulate_histograms(qp, traj_query, seed=seed + 8, traj_offset=2**31)   # SSA-vs-SSA noise floor
+    torch.cuda.synchronize()
+    feats_q = torch.from_numpy(standardise(qp)).cuda()
+    net.predict(feats_q)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 20
+    for _ in range(reps):
+        net.predict(feats_q)
+    torch.cuda.synchronize()
+    nn_s = (time.perf_counter() - t0) / reps
+    answer, w1, fallback = serve(net, qp, judge)
+    noise = ssa.hist_w1(twin, judge)
+    w1_ans = ssa.hist_w1(answer, twin)
+    torch.cuda.synchronize()
+    w1n, noisen = w1.cpu().numpy(), noise.cpu().numpy()
+    report.update({
+        "ssa_query_s": ssa_s, "surrogate_query_s": nn_s, "speedup_vs_ssa": ssa_s / nn_s,
+        "w1_surrogate_median": float(np.median(w1n)), "w1_surrogate_mean": float(w1n.mean()),
+        "w1_ssa_noise_median": float(np.median(noisen)), "fallback_fraction": float(fallback.float().mean()),
+        "w1_answer_vs_twin_mean": float(w1_ans.mean()),
+    })
+    net.close()
+    return report
+
+
+if __name__ == "__main__":
+    kw = {}
+    for arg in sys.argv[1:]:
+        k, v = arg.split("=")
+        kw[k] = int(v)
+    print(json.dumps(run(**kw)), flush=True)

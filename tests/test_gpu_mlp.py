@@ -34,3 +34,75 @@ def test_gemm_matches_fp32_reference(ssa, M, N, K):
     bound = K * 2.0 ** -23 * (A.double().abs() @ B.double().abs().T) + 1e-30
     err = (D.double() - ref).abs()
     assert torch.all(err <= bound), float((err / bound).max())
+
+
+def _features_targets(B, seed):
+    rng = np.random.default_rng(seed)
+    feats = rng.uniform(-1, 1, size=(B, 4)).astype(np.float32)
+    lam = np.exp(2.0 + feats[:, 0] + 0.5 * feats[:, 2])          # a smooth family of laws
+    k = np.arange(128)
+    import scipy.stats
+    t = scipy.stats.poisson.pmf(k[None, :], lam[:, None])
+    t[:, -1] += 1.0 - t.sum(axis=1)
+    return feats, t.astype(np.float32)
+
+
+def test_surrogate_forward_and_gradients_match_oracle(ssa):
+    """GPU forward/backward against the float64 oracle that rounds to bf16 at
+    the same storage points; the remaining difference is fp32 summation order
+    and rare one-ulp bf16 rounding flips: relative error per parameter block
+    <= 2e-2, loss within 1e-3."""
+    from oracle import mlp
+    net = ssa.Surrogate(max_batch=1024, seed=7)
+    theta = net.get_params().astype(np.float64)
+    assert theta.size == mlp.N_PARAMS and np.all(mlp.unflatten(theta)["W1"][:, 4:] == 0)
+    B = 300
+    feats, t = _features_targets(B, 1)
+    f_d, t_d = torch.from_numpy(feats).cuda(), torch.from_numpy(t).cuda()
+    probs = net.predict(f_d).cpu().numpy()
+    q, _ = mlp.forward(theta, feats.astype(np.float64), bf16=True)
+    assert np.max(np.abs(probs - q)) < 2e-3
+    loss, g = net.gradients(f_d, t_d)
+    lo, go = mlp.loss_and_grad(theta, feats.astype(np.float64), t.astype(np.float64), bf16=True)
+    assert abs(loss - lo) < 1e-3 * max(1.0, abs(lo))
+    at = 0
+    for name, shape in mlp.SHAPES:
+        n = int(np.prod(shape))
+        a, b = g[at:at + n].astype(np.float64), go[at:at + n]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+        assert rel < 2e-2, (name, rel)
+        at += n
+    net.status()
+
+
+def test_surrogate_training_reduces_loss(ssa):
+    net = ssa.Surrogate(max_batch=512, seed=3)
+    feats, t = _features_targets(4096, 2)
+    f_d, t_d = torch.from_numpy(feats).cuda(), torch.from_numpy(t).cuda()
+    loss = torch.zeros(1, device="cuda")
+    first = None
+    for step in range(400):
+        i = (step * 512) % 4096
+        net.train_step(f_d[i:i + 512], t_d[i:i + 512], lr=1e-3, loss=loss)
+        if step == 0:
+            torch.cuda.synchronize()
+            first = float(loss)
+    torch.cuda.synchronize()
+    last = float(loss)
+    net.status()
+    entropy = float(-(t * np.log(np.maximum(t, 1e-30))).sum(axis=1).mean())
+    assert last < first and (last - entropy) < 0.25 * (first - entropy), (first, last, entropy)
+
+
+def test_histogram_and_w1_kernels(ssa):
+    rng = np.random.default_rng(4)
+    counts = rng.poisson(20, size=(37, 300)).astype(np.int32)
+    counts[0, :5] = 500       # clamped into the last bin
+    c_d = torch.from_numpy(counts).cuda().reshape(-1)
+    h = ssa.histogram(c_d, 37, 300).cpu().numpy()
+    ref = np.stack([np.bincount(np.minimum(r, 127), minlength=128) / 300.0 for r in counts])
+    np.testing.assert_allclose(h, ref, rtol=0, atol=1e-7)
+    q = np.roll(ref, 1, axis=1)
+    w = ssa.hist_w1(torch.from_numpy(ref.astype(np.float32)).cuda(), torch.from_numpy(q.astype(np.float32)).cuda())
+    from oracle import mlp
+    np.testing.assert_allclose(w.cpu().numpy(), mlp.wasserstein_hist(ref, q), rtol=1e-4, atol=1e-5)

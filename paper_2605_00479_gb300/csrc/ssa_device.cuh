@@ -216,6 +216,47 @@ __device__ __forceinline__ float sr16(float x, uint32_t rbits, bool hi)
     return widen16<FMT>((uint16_t)(hi ? (d >> 16) : (d & 0xFFFFu)));
 }
 
+// Native round-to-nearest 16-bit arithmetic on bit patterns.  For +, -, *
+// and / the binary32 result rounded once to binary16 or bfloat16 equals the
+// correctly rounded 16-bit result (binary32 has at least 2p+2 significand
+// bits for both formats), so these give exactly the contract's RN values.
+template <int FMT>
+struct Native16 {
+    __device__ static __forceinline__ uint16_t from_int(int v)
+    {
+        uint16_t h;
+        if constexpr (FMT == 0) {
+            asm("cvt.rn.f16.s32 %0, %1;" : "=h"(h) : "r"(v));
+        } else {
+            const float f = (float)v;   // exact below 2^24; rounded as the contract says above
+            asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(f));
+        }
+        return h;
+    }
+    __device__ static __forceinline__ uint16_t from_f32(float v)
+    {
+        uint16_t h;
+        if constexpr (FMT == 0) asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(v));
+        else asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(v));
+        return h;
+    }
+    __device__ static __forceinline__ float to_f32(uint16_t h) { return widen16<FMT>(h); }
+    __device__ static __forceinline__ uint16_t mul(uint16_t a, uint16_t b)
+    {
+        uint16_t d;
+        if constexpr (FMT == 0) asm("mul.rn.f16 %0, %1, %2;" : "=h"(d) : "h"(a), "h"(b));
+        else asm("mul.rn.bf16 %0, %1, %2;" : "=h"(d) : "h"(a), "h"(b));
+        return d;
+    }
+    __device__ static __forceinline__ uint16_t add(uint16_t a, uint16_t b)
+    {
+        uint16_t d;
+        if constexpr (FMT == 0) asm("add.rn.f16 %0, %1, %2;" : "=h"(d) : "h"(a), "h"(b));
+        else asm("add.rn.bf16 %0, %1, %2;" : "=h"(d) : "h"(a), "h"(b));
+        return d;
+    }
+};
+
 // ------------------------------------------------------------ mode traits
 template <int PREC>
 struct ModeTraits {
@@ -355,6 +396,7 @@ struct Lane {
     P c[Model::M];       // c'_j in the propensity type
     P h0[Model::M];      // alpha0 (Hill rows)
     P h1[Model::M];      // alpha  (Hill rows)
+    uint16_t c16[Model::M], h016[Model::M], h116[Model::M];   // bit patterns (RN 16-bit modes)
     P t;
     P s_next;            // next sample time (or +inf)
     int64_t n;           // events fired
@@ -453,6 +495,14 @@ __device__ void init_lane(const RunArgs &a, Lane<Model, PREC> &L, int64_t item, 
             L.h1[j] = P(0);
         }
     });
+    if constexpr (ModeTraits<PREC>::k16) {
+        unroll<Model::M>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            L.c16[j] = Native16<ModeTraits<PREC>::kFmt>::from_f32(L.c[j]);
+            L.h016[j] = Native16<ModeTraits<PREC>::kFmt>::from_f32(L.h0[j]);
+            L.h116[j] = Native16<ModeTraits<PREC>::kFmt>::from_f32(L.h1[j]);
+        });
+    }
     L.t = P(0);
     L.n = 0;
     L.k = 0;
@@ -492,7 +542,39 @@ __device__ __forceinline__ void ssa_step(const RunArgs &a, Lane<Model, PREC> &L,
 
     // 1. propensities a_j (Sec. 2 step 1), in the propensity type
     P prop[M];
-    unroll<M>([&](auto J) {
+    if constexpr (Tr::k16 && !SR) {
+        using H = Native16<Tr::kFmt>;
+        unroll<M>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            if (Model::template law<j>(a) == 1) {
+                const int reg = Model::template hill_reg<j>(a);
+                int xr = 0;
+                unroll<Model::N>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    if (i == reg) xr = L.x[i];
+                });
+                const uint16_t Pv = H::from_int(xr);
+                uint16_t q = Pv;
+                const int h = Model::template hill_h<j>(a);
+                for (int m = 1; m < h; ++m) q = H::mul(q, Pv);
+                const uint16_t d = H::add(H::from_f32(1.0f), q);
+                const uint16_t f = H::from_f32(H::to_f32(L.h116[j]) / H::to_f32(d));
+                prop[j] = H::to_f32(H::add(L.h016[j], f));
+            } else {
+                uint16_t av = L.c16[j];
+                bool zero = false;
+                unroll<Model::N>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    const int r = Model::template order<j, i>(a);
+                    if (r > 0 && !Model::template folded<j, i>(a)) {
+                        zero = zero || (L.x[i] < r);
+                        for (int m = 0; m < r; ++m) av = H::mul(av, H::from_int(L.x[i] - m));
+                    }
+                });
+                prop[j] = zero ? P(0) : H::to_f32(av);
+            }
+        });
+    } else unroll<M>([&](auto J) {
         constexpr int j = decltype(J)::value;
         prop[j] = P(0);
         if (!Model::template active<j>(a)) return;
@@ -602,17 +684,21 @@ __device__ __forceinline__ void ssa_step(const RunArgs &a, Lane<Model, PREC> &L,
 
     // 4c. integer state update x += nu_mu, clock t = t_new
     bool negative = false;
-    unroll<M>([&](auto J) {
-        constexpr int j = decltype(J)::value;
-        if (mu == j) {
-            unroll<Model::N>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                const int d = Model::template nu<j, i>(a);
-                if (d != 0) {
-                    L.x[i] += d;
-                    negative = negative || (L.x[i] < 0);
-                }
-            });
+    unroll<Model::N>([&](auto I) {       // branch-free: d_i = nu[mu][i] by selects
+        constexpr int i = decltype(I)::value;
+        int d = 0;
+        bool moves = false;
+        unroll<M>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            const int v = Model::template nu<j, i>(a);
+            if (v != 0) {
+                d = (mu == j) ? v : d;
+                moves = true;
+            }
+        });
+        if (moves) {
+            L.x[i] += d;
+            negative = negative || (L.x[i] < 0);
         }
     });
     L.t = t_new;

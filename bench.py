@@ -33,6 +33,8 @@ from paper_2605_00479_gb300 import presets as P  # noqa: E402
 METRIC = "SSA reaction events/s on 1 GB300, 16-bit modes vs fp64, at KS p>0.05 vs oracle"
 MODES16 = [("mixed_f16", "rn"), ("mixed_bf16", "rn"), ("uniform_f16", "rn"), ("uniform_f16", "sr"),
            ("uniform_bf16", "sr")]
+# reported beside the step (timed alone, not part of the timed step): selective SR
+EXTRA_MODES = [("uniform_f16", "sra"), ("uniform_bf16", "sra")]
 N_TRAJ = 1_000_000
 T_END = 10.0
 K_SAMPLES = 50
@@ -74,7 +76,35 @@ def ops_per_event(prec, rnd):
     if rnd == "sr":
         n_sr = SCHLOGL_FACTORS * 2 + (M_REACTIONS - 1 + 5 if prec.startswith("uniform") else 0)
         ops += philox * ((n_sr + 7) // 8)   # stochastic-rounding blocks per step
+    if rnd == "sra":
+        ops += philox * ((M_REACTIONS + 7) // 8)   # sums and clock only
     return float(ops)
+
+
+# ------------------------------------------------------------ ncu traffic
+# DRAM bytes (read + write) per trajectory of the step's kernels, from one ncu
+# capture (profiles/ssa_kernel_schlogl_*.md; a 3e5-trajectory launch scaled
+# per trajectory: the traffic is the snapshot stream, proportional to the
+# trajectories).  Valid only for the kernel source it was measured on: the
+# key includes a hash of the device code, and a changed kernel reports null.
+NCU_TRAFFIC_PER_TRAJ = {
+    # uniform_f16 RN, 3e5 trajectories: 279,794,432 B read + 443,069,184 B written
+    ("d6789f7569202092", "uniform_f16:rn"): (279794432 + 443069184) / 300000,
+}
+
+
+def device_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("ssa_device.cuh", "ssa_models.h", "ssa_launch.h"):
+        with open(os.path.join(ROOT, "paper_2605_00479_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(mode_key, n_traj):
+    v = NCU_TRAFFIC_PER_TRAJ.get((device_source_hash(), mode_key))
+    return None if v is None else v * n_traj
 
 
 # ------------------------------------------------------------------ clocks
@@ -226,35 +256,71 @@ def run_ours(args, world, rank, local):
     model = ssa.Model.from_dict(m_dict)
     offset = rank * N_TRAJ
     dev = torch.device("cuda", local)
-    out = torch.empty((K_SAMPLES, model.N, N_TRAJ), dtype=torch.int32, device=dev)
-    status = torch.empty(N_TRAJ, dtype=torch.int32, device=dev)
-    nev = torch.empty(N_TRAJ, dtype=torch.int64, device=dev)
-    tfin = torch.empty(N_TRAJ, dtype=torch.float64, device=dev)
-    stream = torch.cuda.current_stream()
+    modes_all = MODES16 + EXTRA_MODES + [("fp64", "rn")]
+    # one output set per mode, so that the modes of a step can run concurrently
+    bufs = {m: (torch.empty((K_SAMPLES, model.N, N_TRAJ), dtype=torch.int32, device=dev),
+                torch.empty(N_TRAJ, dtype=torch.int32, device=dev),
+                torch.empty(N_TRAJ, dtype=torch.int64, device=dev),
+                torch.empty(N_TRAJ, dtype=torch.float64, device=dev)) for m in modes_all}
+    streams = {m: torch.cuda.Stream() for m in modes_all}
+    main = torch.cuda.current_stream()
 
-    def launch(prec, rnd, seed):
-        ssa.ensemble_run(model, N_TRAJ, x0, T_END, samples, prec, rnd, True, seed, MAX_EVENTS, 4, out=out,
+    def launch(m, seed, stream):
+        out, status, nev, tfin = bufs[m]
+        ssa.ensemble_run(model, N_TRAJ, x0, T_END, samples, m[0], m[1], True, seed, MAX_EVENTS, 4, out=out,
                          status=status, n_events=nev, t_final=tfin, stream=stream, traj_offset=offset)
 
-    def one_step(modes, seed, record):
+    def record_results(modes, record):
+        for m in modes:
+            out, status, nev, _ = bufs[m]
+            record.setdefault(m, []).append((nev.sum(), out[-1, 0].clone(), status.clone()))
+
+    def sequential_step(modes, seed, record):
+        """Modes one after the other on the main stream, each timed alone."""
         per = []
-        for prec, rnd in modes:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            launch(prec, rnd, seed)
-            e1.record(stream)
-            per.append((prec, rnd, e0, e1))
-            if record is not None:
-                # event totals and final states, read after the launch (outside the kernel's events)
-                record.setdefault((prec, rnd), []).append((nev.sum(), out[-1, 0].clone(), status.clone()))
+        for m in modes:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(main)
+            launch(m, seed, main)
+            e1.record(main)
+            per.append((m, e0, e1))
+        if record is not None:
+            record_results(modes, record)
         return per
 
-    # warm-up (untimed)
-    for _ in range(args.warmup):
-        one_step(MODES16, SEED, None)
-    one_step([("fp64", "rn")], SEED_FP64, None)
+    def concurrent_step(modes, seed, record):
+        """All modes at once on their own streams: the end-of-queue tail of one
+        persistent kernel overlaps the start of the next."""
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(main)
+        per = []
+        for m in modes:
+            s = streams[m]
+            s.wait_event(start)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            launch(m, seed, s)
+            e1.record(s)
+            per.append((m, e0, e1))
+        for m in modes:
+            main.wait_stream(streams[m])
+        stop.record(main)
+        if record is not None:
+            record_results(modes, record)
+        return start, stop, per
+
+    # warm-up (untimed): concurrent steps, then one sequential pass that gives
+    # each mode's own rate, and the fp64 reference
+    for _ in range(max(0, args.warmup - 1)):
+        if (not args.concurrent):
+            sequential_step(MODES16, SEED, None)
+        else:
+            concurrent_step(MODES16, SEED, None)
+    rec_alone = {}
+    alone = sequential_step(MODES16 + EXTRA_MODES, SEED, rec_alone)
+    sequential_step([("fp64", "rn")], SEED_FP64, None)
     torch.cuda.synchronize()
+    alone_ms = {m: e0.elapsed_time(e1) for m, e0, e1 in alone}
 
     # timed: K steps of the five 16-bit modes
     clocks = ClockSampler(local)
@@ -263,29 +329,42 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     rec = {}
     t0 = time.perf_counter()
-    steps = [one_step(MODES16, SEED, rec) for _ in range(args.steps)]
+    if (not args.concurrent):
+        steps = [sequential_step(MODES16, SEED, rec) for _ in range(args.steps)]
+    else:
+        steps = [concurrent_step(MODES16, SEED, rec) for _ in range(args.steps)]
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     barrier(world)
     clocks.stop()
     kernel_ms = {}
-    for per in steps:
-        for prec, rnd, e0, e1 in per:
-            kernel_ms.setdefault((prec, rnd), []).append(e0.elapsed_time(e1))
-    step_ms = [sum(e0.elapsed_time(e1) for _, _, e0, e1 in per) for per in steps]
+    if (not args.concurrent):
+        step_ms = []
+        for per in steps:
+            for m, e0, e1 in per:
+                kernel_ms.setdefault(m, []).append(e0.elapsed_time(e1))
+            step_ms.append(sum(e0.elapsed_time(e1) for _, e0, e1 in per))
+    else:
+        step_ms = []
+        for start, stop, per in steps:
+            for m, e0, e1 in per:
+                kernel_ms.setdefault(m, []).append(e0.elapsed_time(e1))
+            step_ms.append(start.elapsed_time(stop))
     local_time = sum(step_ms) / 1e3
     events = {k: float(sum(float(v[0]) for v in vals)) for k, vals in rec.items()}
     local_events = sum(events.values())
 
     # fp64 beside it, same number of launches
     rec64 = {}
-    steps64 = [one_step([("fp64", "rn")], SEED_FP64, rec64) for _ in range(args.steps)]
+    steps64 = [sequential_step([("fp64", "rn")], SEED_FP64, rec64) for _ in range(args.steps)]
     torch.cuda.synchronize()
-    fp64_ms = [e0.elapsed_time(e1) for per in steps64 for _, _, e0, e1 in per]
+    fp64_ms = [e0.elapsed_time(e1) for per in steps64 for _, e0, e1 in per]
     fp64_events = sum(float(v[0]) for v in rec64[("fp64", "rn")])
     fp64_rate = fp64_events / (sum(fp64_ms) / 1e3)
+    model_out = bufs[MODES16[0]]
 
     # end to end through the host-buffer entry point (pinned host memory)
+    del model_out
     h_out = torch.empty((K_SAMPLES, model.N, N_TRAJ), dtype=torch.int32).pin_memory()
     h_st = torch.empty(N_TRAJ, dtype=torch.int32).pin_memory()
     h_ev = torch.empty(N_TRAJ, dtype=torch.int64).pin_memory()
@@ -318,19 +397,31 @@ def run_ours(args, world, rank, local):
         xs = vals[-1][1].cpu().numpy()
         st = vals[-1][2].cpu().numpy()
         D, p = stats.ks_2samp(ref, xs)
-        ms = kernel_ms[(prec, rnd)]
-        rate = events[(prec, rnd)] / (sum(ms) / 1e3)
+        D4, p4 = stats.ks_2samp(ref[:10000], xs[:10000])
+        ev_alone = float(rec_alone[(prec, rnd)][0][0])
+        rate = ev_alone / (alone_ms[(prec, rnd)] / 1e3)
         modes_out[f"{prec}:{rnd}"] = {
-            "events_per_s": rate, "ms_per_launch": float(np.mean(ms)), "speedup_vs_fp64": rate / fp64_rate,
-            "ks_p_vs_fp64": p, "w1_vs_fp64": stats.wasserstein1(ref, xs), "mean": float(xs.mean()),
-            "var": float(xs.var()), "frac_max_events": float(np.mean((st & 2) != 0)),
+            "events_per_s": rate, "ms_per_launch_alone": alone_ms[(prec, rnd)],
+            "ms_per_launch_in_step": float(np.mean(kernel_ms[(prec, rnd)])), "speedup_vs_fp64": rate / fp64_rate,
+            "ks_p_vs_fp64": p, "ks_p_vs_fp64_n1e4": p4, "w1_vs_fp64": stats.wasserstein1(ref, xs),
+            "mean": float(xs.mean()), "var": float(xs.var()), "frac_max_events": float(np.mean((st & 2) != 0)),
             "ops_per_event": ops_per_event(prec, rnd)}
+    for prec, rnd in EXTRA_MODES:
+        out_x, st_x = bufs[(prec, rnd)][0], bufs[(prec, rnd)][1]
+        xs = rec_alone[(prec, rnd)][0][1].cpu().numpy()
+        ev_alone = float(rec_alone[(prec, rnd)][0][0])
+        rate = ev_alone / (alone_ms[(prec, rnd)] / 1e3)
+        modes_out[f"{prec}:{rnd}"] = {
+            "events_per_s": rate, "ms_per_launch_alone": alone_ms[(prec, rnd)], "in_step": False,
+            "speedup_vs_fp64": rate / fp64_rate, "ks_p_vs_fp64": stats.ks_2samp(ref, xs)[1],
+            "ks_p_vs_fp64_n1e4": stats.ks_2samp(ref[:10000], xs[:10000])[1], "w1_vs_fp64": stats.wasserstein1(ref, xs),
+            "mean": float(xs.mean()), "var": float(xs.var()), "ops_per_event": ops_per_event(prec, rnd)}
     modes_out["fp64:rn"] = {"events_per_s": fp64_rate, "ms_per_launch": float(np.mean(fp64_ms)),
                             "mean": float(ref.mean()), "var": float(ref.var())}
 
     # roofline of the dominant kernel (largest share of the step)
     dom = max(kernel_ms, key=lambda k: sum(kernel_ms[k]))
-    dom_ms = float(np.mean(kernel_ms[dom]))
+    dom_ms = float(np.mean(kernel_ms[dom]))     # on its own stream, inside the timed steps
     dom_events = events[dom] / args.steps
     clk = clocks.summary()
     sm_mhz = clk["sm_mhz"] or 1455.0
@@ -345,7 +436,8 @@ def run_ours(args, world, rank, local):
         "gpu_launches": len(MODES16) * args.steps,
         "roofline": {"bound": "alu", "kernel": f"ssa_kernel<schlogl,{dom[0]},{dom[1]}>",
                      "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
-                     "frac": achieved_gops / peak_gops, "traffic": None,
+                     "frac": achieved_gops / peak_gops, "traffic": traffic_per_launch(f"{dom[0]}:{dom[1]}", N_TRAJ),
+                     "traffic_unit": "bytes per launch", "source_hash": device_source_hash(),
                      "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock sampled in the run)",
                      "snapshot_hbm_gbs": (K_SAMPLES * model.N * N_TRAJ * 4) / (dom_ms / 1e3) / 1e9},
         "fp64_events_per_s": fp64_rate_job, "speedup_vs_fp64": value / fp64_rate_job,
@@ -372,6 +464,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--concurrent", action="store_true",
+                    help="run the modes of a step on concurrent streams (overlaps the kernels' end-of-queue tails)")
     ap.add_argument("--n-traj", type=int, default=None,
                     help="trajectories per GPU (default 10^6; smaller values are for profiling only)")
     ap.add_argument("--modes", default=None, help="comma list like mixed_f16:rn (profiling only)")

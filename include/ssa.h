@@ -63,8 +63,12 @@ typedef enum {
 
 /* Rounding of 16-bit operations (Sec. 3.3): round-to-nearest-even, or
  * stochastic rounding applied after every operation whose result has the
- * 16-bit type.  SR is valid only with the four 16-bit modes. */
-typedef enum { SSA_RN = 0, SSA_SR = 1 } ssa_rounding;
+ * 16-bit type (valid with the four 16-bit modes), or selective stochastic
+ * rounding: SR only at the accumulation points -- the partial sums of the
+ * propensities and the clock update -- and round-to-nearest elsewhere (the
+ * strategy Sec. 3.3 names without testing; valid with the uniform modes,
+ * since mixed modes accumulate in binary32). */
+typedef enum { SSA_RN = 0, SSA_SR = 1, SSA_SR_ACCUM = 2 } ssa_rounding;
 
 typedef enum {
     SSA_OK = 0, SSA_EINVAL = -1, SSA_ENOMEM = -2, SSA_ECUDA = -3, SSA_ETIMEDOUT = -4

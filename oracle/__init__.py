@@ -28,7 +28,7 @@ from . import build as _build
 _LIB = None
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "mixed_f16": 2, "mixed_bf16": 3, "uniform_f16": 4, "uniform_bf16": 5}
-ROUNDINGS = {"rn": 0, "sr": 1}
+ROUNDINGS = {"rn": 0, "sr": 1, "sra": 2}   # sra: SR at accumulation points only
 STATUS_OVERFLOW, STATUS_MAX_EVENTS, STATUS_STATE_RANGE, STATUS_NAN = 1, 2, 4, 8
 
 

@@ -68,6 +68,11 @@
  *      t_new = rnd(t + tau).  SR operation order within a step: propensity
  *      chains (reaction order), partial sums S_1..S_{M-1}, E, U2, tau,
  *      target, t_new.
+ *   R7b selective SR (rounding = 2, uniform modes only; the paper names the
+ *      strategy, "SR applied only at accumulation points", without testing
+ *      it): the partial sums S_1..S_{M-1} and t_new are rounded
+ *      stochastically, every other operation by RN.  These M operations use
+ *      SR slots 0..M-1 of the step (B = ceil(M/8) blocks).
  *   R8 log: own implementation, ln x = e ln2 + 2 atanh(s), s = (m-1)/(m+1),
  *      m in [sqrt(1/2), sqrt(2)], odd atanh series to s^9 (binary32) or s^23
  *      (binary64), Cody-Waite split of ln2, Horner order fixed below.
@@ -628,12 +633,18 @@ static void traj_uniform(const omodel *md, const runp *rp, word_stream *ws, word
         nsr += chain_ops(md, j);
     }
     nsr += (M - 1) + 5;   /* partial sums, E, U2, tau, target, t_new */
+    if (sr == 2) nsr = M; /* selective SR: partial sums and t_new only */
     const uint64_t Ws = 4u * (uint64_t)((nsr + 7) / 8);   /* SR words per step: whole blocks */
     float t_end = rn16(fmt, (float)rp->t_end);
     float smp[1024];
     for (int kk = 0; kk < rp->K; ++kk) smp[kk] = rn16(fmt, (float)rp->samples[kk]);
-    rounder R;
-    R.bf16 = fmt; R.sr = sr; R.ws = wsr; R.sr_base = 0; R.op = 0;
+    /* R rounds the propensity chains and the variates; A the accumulation
+     * points (the same rounder unless SR is selective) */
+    rounder R, Racc;
+    R.bf16 = fmt; R.sr = sr == 1; R.ws = wsr; R.sr_base = 0; R.op = 0;
+    Racc = R;
+    Racc.sr = sr != 0;
+    rounder *A = sr == 2 ? &Racc : &R;
     float t = 0.0f;
     int64_t n = 0;
     int k = 0;
@@ -642,9 +653,11 @@ static void traj_uniform(const omodel *md, const runp *rp, word_stream *ws, word
         uint64_t w = (uint64_t)n * 2u;
         R.sr_base = (uint64_t)n * Ws;
         R.op = 0;
+        Racc.sr_base = R.sr_base;
+        Racc.op = 0;
         for (int j = 0; j < M; ++j) a[j] = prop_16(md, j, x, cp, h0, h1, &R);
         Ssum[0] = a[0];
-        for (int j = 1; j < M; ++j) Ssum[j] = rnd16(&R, Ssum[j - 1] + a[j]);
+        for (int j = 1; j < M; ++j) Ssum[j] = rnd16(A, Ssum[j - 1] + a[j]);
         float a0 = Ssum[M - 1];
         if (f32_is_nan(a0)) { *status |= ST_NAN; break; }
         if (f32_is_inf(a0)) { *status |= ST_OVERFLOW; break; }
@@ -656,7 +669,7 @@ static void traj_uniform(const omodel *md, const runp *rp, word_stream *ws, word
         float U2 = rnd16(&R, u2);
         float tau = rnd16(&R, E / a0);
         float target = rnd16(&R, U2 * a0);
-        float t_new = rnd16(&R, t + tau);
+        float t_new = rnd16(A, t + tau);
         while (k < rp->K && smp[k] < t_new) write_snapshot(S, k++, x, status);
         if (t_new > t_end) break;
         int mu = -1;
@@ -685,8 +698,9 @@ int oracle_run(int N, int M, const int32_t *order, const int32_t *stoich, const 
                void *out, uint32_t *status, int64_t *n_events, double *t_final)
 {
     if (N < 1 || N > OR_MAX_N || M < 1 || M > OR_MAX_M || K < 0 || K > 1024) return -1;
-    if (precision < 0 || precision > 5 || rounding < 0 || rounding > 1) return -1;
+    if (precision < 0 || precision > 5 || rounding < 0 || rounding > 2) return -1;
     if (rounding == 1 && precision < 2) return -1;
+    if (rounding == 2 && precision < 4) return -1;   /* selective SR: uniform modes only */
     if (state_bytes != 2 && state_bytes != 4) return -1;
     if (n_traj < 0 || g0 + (uint64_t)n_traj > 0x100000000ull) return -1;  /* 32-bit trajectory ids */
     omodel md;

@@ -154,8 +154,11 @@ int validate_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, c
         if (k > 0 && s < sample_times[k - 1]) return fail(SSA_EINVAL, "sample_times must be ascending");
     }
     if (precision < SSA_FP64 || precision > SSA_UNIFORM_BF16) return fail(SSA_EINVAL, "unknown precision %d", precision);
-    if (rounding != SSA_RN && rounding != SSA_SR) return fail(SSA_EINVAL, "unknown rounding %d", rounding);
+    if (rounding != SSA_RN && rounding != SSA_SR && rounding != SSA_SR_ACCUM)
+        return fail(SSA_EINVAL, "unknown rounding %d", rounding);
     if (rounding == SSA_SR && precision < SSA_MIXED_F16) return fail(SSA_EINVAL, "stochastic rounding needs a 16-bit mode");
+    if (rounding == SSA_SR_ACCUM && precision < SSA_UNIFORM_F16)
+        return fail(SSA_EINVAL, "selective stochastic rounding needs a uniform 16-bit mode");
     if (max_events < 0) return fail(SSA_EINVAL, "max_events must be >= 0");
     if (state_bytes != 2 && state_bytes != 4) return fail(SSA_EINVAL, "state_bytes must be 2 or 4");
     return SSA_OK;

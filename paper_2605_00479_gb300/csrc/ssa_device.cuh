@@ -26,7 +26,9 @@
 //    operation i uses the low (even i) / high (odd i) half of word i/2.
 //  * Uniform mode rounds, in this order: propensity chains, partial sums
 //    S_1..S_{M-1}, E = rnd(-log u1), U2 = rnd(u2), tau = rnd(E / a0),
-//    target = rnd(U2 * a0), t_new = rnd(t + tau).
+//    target = rnd(U2 * a0), t_new = rnd(t + tau).  Selective SR (uniform
+//    modes) rounds only S_1..S_{M-1} and t_new stochastically, with SR slots
+//    0..M-1, and everything else to nearest.
 //  * log: ln x = e ln2 + 2 atanh(s), s = (m-1)/(m+1), m in [sqrt(1/2),
 //    sqrt(2)], odd series to s^9 (binary32) / s^23 (binary64), ln2 split into
 //    a 16-bit (binary32) or 32-bit (binary64) head and a tail.
@@ -290,6 +292,9 @@ struct SRBits {
 };
 
 // Rounding of one operation result to the propensity / uniform type.
+// SR = 0: round to nearest; 1: stochastic rounding after every operation;
+// 2: stochastic rounding only at the accumulation points (partial sums and
+// the clock), round to nearest elsewhere.
 template <int PREC, int SR>
 struct Rounder {
     using T = ModeTraits<PREC>;
@@ -297,7 +302,16 @@ struct Rounder {
     __device__ __forceinline__ typename T::P rnd(typename T::P x, int op)
     {
         if constexpr (T::k16) {
-            if constexpr (SR) return sr16<T::kFmt>(x, bits.word(op), (op & 1) != 0);
+            if constexpr (SR == 1) return sr16<T::kFmt>(x, bits.word(op), (op & 1) != 0);
+            else return rn16<T::kFmt>(x);
+        } else {
+            return x;
+        }
+    }
+    __device__ __forceinline__ typename T::P rnd_acc(typename T::P x, int op)
+    {
+        if constexpr (T::k16) {
+            if constexpr (SR != 0) return sr16<T::kFmt>(x, bits.word(op), (op & 1) != 0);
             else return rn16<T::kFmt>(x);
         } else {
             return x;
@@ -531,7 +545,8 @@ __device__ __forceinline__ void ssa_step(const RunArgs &a, Lane<Model, PREC> &L,
     Rounder<PREC, SR> R;
     int sr_total = 0;
     if constexpr (Tr::k16 && SR) {
-        sr_total = Model::total_chain_ops(a) + (Tr::kUniform ? (Model::last(a) + 5) : 0);
+        sr_total = SR == 2 ? Model::last(a) + 1
+                           : Model::total_chain_ops(a) + (Tr::kUniform ? (Model::last(a) + 5) : 0);
         const int B = (sr_total + 7) >> 3;
         R.bits.base = (uint64_t)L.n * (uint64_t)B;
         R.bits.traj = L.traj;
@@ -542,7 +557,7 @@ __device__ __forceinline__ void ssa_step(const RunArgs &a, Lane<Model, PREC> &L,
 
     // 1. propensities a_j (Sec. 2 step 1), in the propensity type
     P prop[M];
-    if constexpr (Tr::k16 && !SR) {
+    if constexpr (Tr::k16 && SR != 1) {
         using H = Native16<Tr::kFmt>;
         unroll<M>([&](auto J) {
             constexpr int j = decltype(J)::value;
@@ -615,14 +630,14 @@ __device__ __forceinline__ void ssa_step(const RunArgs &a, Lane<Model, PREC> &L,
     P S[M];
     P a0 = P(0);
     {
-        int op = Model::total_chain_ops(a);
+        int op = SR == 2 ? 0 : Model::total_chain_ops(a);
         unroll<M>([&](auto J) {
             constexpr int j = decltype(J)::value;
             if (!Model::template active<j>(a)) { S[j] = a0; return; }
             if constexpr (j == 0) {
                 S[0] = prop[0];
             } else {
-                if constexpr (Tr::kUniform) S[j] = R.rnd(S[j - 1] + prop[j], op++);
+                if constexpr (Tr::kUniform) S[j] = R.rnd_acc(S[j - 1] + prop[j], op++);
                 else S[j] = S[j - 1] + prop[j];
             }
             a0 = S[j];
@@ -652,7 +667,7 @@ __device__ __forceinline__ void ssa_step(const RunArgs &a, Lane<Model, PREC> &L,
             const float U2 = R.rnd(u2, op++);
             tau = R.rnd(E / a0, op++);
             target = R.rnd(U2 * a0, op++);
-            t_new = R.rnd(L.t + tau, op++);
+            t_new = R.rnd_acc(L.t + tau, SR == 2 ? Model::last(a) : op);
         } else {
             const float E = -log_f32(u1);
             tau = E / a0;
@@ -729,7 +744,7 @@ __device__ __noinline__ void ssa_step_general(const RunArgs &a, Lane<GeneralMode
     }
     Rounder<PREC, SR> R;
     if constexpr (Tr::k16 && SR) {
-        const int sr_total = a.sr_ops + (Tr::kUniform ? (a.M - 1 + 5) : 0);
+        const int sr_total = SR == 2 ? a.M : a.sr_ops + (Tr::kUniform ? (a.M - 1 + 5) : 0);
         R.bits.base = (uint64_t)L.n * (uint64_t)((sr_total + 7) >> 3);
         R.bits.traj = L.traj;
         R.bits.k0 = a.key0;
@@ -769,10 +784,10 @@ __device__ __noinline__ void ssa_step_general(const RunArgs &a, Lane<GeneralMode
     P S[kMaxM];
     S[0] = prop[0];
     {
-        int op = a.sr_ops;
+        int op = SR == 2 ? 0 : a.sr_ops;
 #pragma unroll 1
         for (int j = 1; j < a.M; ++j) {
-            if constexpr (Tr::kUniform) S[j] = R.rnd(S[j - 1] + prop[j], op++);
+            if constexpr (Tr::kUniform) S[j] = R.rnd_acc(S[j - 1] + prop[j], op++);
             else S[j] = S[j - 1] + prop[j];
         }
     }
@@ -798,7 +813,7 @@ __device__ __noinline__ void ssa_step_general(const RunArgs &a, Lane<GeneralMode
             const float U2 = R.rnd(u2, op++);
             tau = R.rnd(E / a0, op++);
             target = R.rnd(U2 * a0, op++);
-            t_new = R.rnd(L.t + tau, op++);
+            t_new = R.rnd_acc(L.t + tau, SR == 2 ? a.M - 1 : op);
         } else {
             const float E = -log_f32(u1);
             tau = E / a0;

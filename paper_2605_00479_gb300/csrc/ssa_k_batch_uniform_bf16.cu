@@ -8,6 +8,7 @@ cudaError_t launch_batch_uniform_bf16(const BatchArgs &b, int64_t work, int prec
 {
     if (prec == UNIFORM_BF16 && sr == 0) return launch_batch_mode<UNIFORM_BF16, 0>(b, work, compact, cfg, s, grid);
     if (prec == UNIFORM_BF16 && sr == 1) return launch_batch_mode<UNIFORM_BF16, 1>(b, work, compact, cfg, s, grid);
+    if (prec == UNIFORM_BF16 && sr == 2) return launch_batch_mode<UNIFORM_BF16, 2>(b, work, compact, cfg, s, grid);
     return cudaErrorInvalidValue;
 }
 

@@ -39,8 +39,14 @@ cudaError_t launch_family(const RunArgs &a, int prec, int sr, LaunchConfig cfg, 
     case FP32: k = ssa_kernel<ModelF, FP32, 0>; break;
     case MIXED_F16: k = sr ? ssa_kernel<ModelF, MIXED_F16, 1> : ssa_kernel<ModelF, MIXED_F16, 0>; break;
     case MIXED_BF16: k = sr ? ssa_kernel<ModelF, MIXED_BF16, 1> : ssa_kernel<ModelF, MIXED_BF16, 0>; break;
-    case UNIFORM_F16: k = sr ? ssa_kernel<ModelF, UNIFORM_F16, 1> : ssa_kernel<ModelF, UNIFORM_F16, 0>; break;
-    case UNIFORM_BF16: k = sr ? ssa_kernel<ModelF, UNIFORM_BF16, 1> : ssa_kernel<ModelF, UNIFORM_BF16, 0>; break;
+    case UNIFORM_F16:
+        k = sr == 2 ? ssa_kernel<ModelF, UNIFORM_F16, 2>
+                    : (sr ? ssa_kernel<ModelF, UNIFORM_F16, 1> : ssa_kernel<ModelF, UNIFORM_F16, 0>);
+        break;
+    case UNIFORM_BF16:
+        k = sr == 2 ? ssa_kernel<ModelF, UNIFORM_BF16, 2>
+                    : (sr ? ssa_kernel<ModelF, UNIFORM_BF16, 1> : ssa_kernel<ModelF, UNIFORM_BF16, 0>);
+        break;
     default: return cudaErrorInvalidValue;
     }
     int dev = 0, sms = 0, per_sm = 0;

@@ -2,6 +2,8 @@
 
     python -m paper_2605_00479_gb300.experiments batch  [sets=10000] [traj=256]
     python -m paper_2605_00479_gb300.experiments scale  [n_traj=1000000] [t_end=1000] [fp64_traj=20000]
+    python -m paper_2605_00479_gb300.experiments tables [scale=1]
+    python -m paper_2605_00479_gb300.experiments sweeps
 
 batch: telegraph (kon, koff log-uniform in [0.05, 5], km in [5, 100], gamma 1),
   dimerisation (k1, k2 log-uniform in [x0.5, x2] around 1e-3, 0.1; M0 = 300)
@@ -14,6 +16,16 @@ scale: repressilator, `n_traj` trajectories to t_end with 200 snapshots
   streamed to HBM; state stored int32 and int16; propensities in fp16
   (mixed_f16), fp32 and fp64 (fp64 on a subsample of `fp64_traj`
   trajectories: GB300's FP64 rate makes the full ensemble take minutes).
+tables: the paper's per-model comparisons (Sec. 4.1-4.5 tables): every precision
+  mode against an independent fp64 ensemble -- KS p, Wasserstein-1, mean and
+  variance of the reported species at t_end -- with the paper's parameter sets
+  and ensemble sizes (x `scale`).  t_end: birth-death 100 (the paper's uniform
+  BF16 RTN mean matches this horizon), Schloegl 10, telegraph 200, dimer 100,
+  repressilator 200.  Uniform RN runs carry an event cap of 10^6 per trajectory
+  (their clocks may stagnate; capped fractions are reported).
+sweeps: the telegraph kon sweep (kon in [1e-3, 1e-1], koff = 0.1, alpha = 5,
+  beta = 1; uniform modes; W1 to fp64) and the repressilator horizon sweep
+  (t_end in {100, 200, 400, 800}; uniform modes; W1 and KS p to fp64).
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -111,10 +123,82 @@ def scale(n_traj=1_000_000, t_end=1000.0, fp64_traj=20000, seed=5):
     return out
 
 
+MODES_ALL = [("fp32", "rn"), ("mixed_f16", "rn"), ("mixed_f16", "sr"), ("mixed_bf16", "rn"), ("mixed_bf16", "sr"),
+             ("uniform_f16", "rn"), ("uniform_f16", "sr"), ("uniform_f16", "sra"), ("uniform_bf16", "rn"),
+             ("uniform_bf16", "sr"), ("uniform_bf16", "sra")]
+
+
+def _final_states(model_dict, x0, n, t_end, prec, rnd, normalise, seed, species, cap=10**6):
+    import torch
+    m = ssa.Model.from_dict(model_dict)
+    r = ssa.ensemble_run(m, n, x0, t_end, [t_end], prec, rnd, normalise, seed, cap, with_t_final=False)
+    torch.cuda.synchronize()
+    x = r["snapshots"][0, species].cpu().numpy()
+    st = r["status"].cpu().numpy()
+    return x, st
+
+
+def _compare(ref, x):
+    from scipy import stats as sst
+    w1 = float(sst.wasserstein_distance(ref, x))
+    p = float(sst.ks_2samp(ref, x).pvalue)
+    return {"ks_p": p, "w1": w1, "mean": float(x.mean()), "var": float(x.var())}
+
+
+def tables(scale=1, seed=11):
+    """Each model of Sec. 4 in every mode against an independent fp64 ensemble."""
+    cases = [
+        ("birth-death (kb=20, kd=1)", P.birth_death(20.0, 1.0), [0], 50000, 100.0, 0, False),
+        ("schlogl (original)", P.schlogl(), P.schlogl_x0(P.schlogl()), 10000, 10.0, 0, False),
+        ("schlogl (rescaled)", P.schlogl_rescaled(), P.schlogl_x0(P.schlogl_rescaled()), 10000, 10.0, 0, False),
+        ("telegraph (underflow stress)", P.telegraph(0.01, 0.1, 5.0, 1.0), P.TELEGRAPH_X0, 50000, 200.0, 2, False),
+        ("telegraph (bimodal)", P.telegraph(0.05, 0.05, 20.0, 1.0), P.TELEGRAPH_X0, 50000, 200.0, 2, False),
+        ("dimer (nA0=100)", P.dimer(1e-3, 0.1), P.dimer_x0(100), 50000, 100.0, 0, False),
+        ("repressilator (paper set)", P.repressilator_paper(), P.REPRESSILATOR_X0, 10000, 200.0, 3, False),
+    ]
+    out = {"note": "each mode vs an independent fp64 ensemble (different seed); x at t_end", "models": {}}
+    for name, md, x0, n, t_end, sp, norm in cases:
+        n = int(n * scale)
+        ref, _ = _final_states(md, x0, n, t_end, "fp64", "rn", norm, seed, sp)
+        row = {"fp64": {"mean": float(ref.mean()), "var": float(ref.var())}}
+        for prec, rnd in MODES_ALL:
+            x, st = _final_states(md, x0, n, t_end, prec, rnd, norm, seed + 1, sp)
+            d = _compare(ref, x)
+            d["overflow"] = float(np.mean((st & 1) != 0))
+            d["capped"] = float(np.mean((st & 2) != 0))
+            row[f"{prec}:{rnd}"] = d
+        out["models"][name] = row
+    return out
+
+
+def sweeps(seed=21):
+    out = {"kon_sweep": {}, "horizon_sweep": {}}
+    modes = [("uniform_f16", "rn"), ("uniform_f16", "sr"), ("uniform_f16", "sra"), ("uniform_bf16", "rn"),
+             ("uniform_bf16", "sr"), ("uniform_bf16", "sra")]
+    for kon in np.logspace(-3, -1, 7):
+        md = P.telegraph(float(kon), 0.1, 5.0, 1.0)
+        ref, _ = _final_states(md, P.TELEGRAPH_X0, 50000, 200.0, "fp64", "rn", False, seed, 2)
+        out["kon_sweep"][f"{kon:.2e}"] = {f"{p}:{r}": _compare(ref, _final_states(md, P.TELEGRAPH_X0, 50000, 200.0, p, r,
+                                                                                  False, seed + 1, 2)[0])["w1"]
+                                          for p, r in modes}
+    rp = P.repressilator_paper()
+    for t_end in (100.0, 200.0, 400.0, 800.0):
+        ref, _ = _final_states(rp, P.REPRESSILATOR_X0, 10000, t_end, "fp64", "rn", False, seed, 3)
+        row = {}
+        for p, r in modes:
+            x, st = _final_states(rp, P.REPRESSILATOR_X0, 10000, t_end, p, r, False, seed + 1, 3, cap=4 * 10**6)
+            d = _compare(ref, x)
+            d["capped"] = float(np.mean((st & 2) != 0))
+            row[f"{p}:{r}"] = d
+        out["horizon_sweep"][f"{t_end:g}"] = row
+    return out
+
+
 if __name__ == "__main__":
     cmd = sys.argv[1]
     kw = {}
     for arg in sys.argv[2:]:
         k, v = arg.split("=")
-        kw[k] = float(v) if k == "t_end" else int(v)
-    print(json.dumps({"batch": batch, "scale": scale}[cmd](**kw)), flush=True)
+        kw[k] = float(v) if k in ("t_end", "scale") else int(v)
+    fn = {"batch": batch, "scale": scale, "tables": tables, "sweeps": sweeps}[cmd]
+    print(json.dumps(fn(**kw)), flush=True)

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libssa_gb300.so")
 
 PRECISION = {"fp64": 0, "fp32": 1, "mixed_f16": 2, "mixed_bf16": 3, "uniform_f16": 4, "uniform_bf16": 5}
-ROUNDING = {"rn": 0, "sr": 1}
+ROUNDING = {"rn": 0, "sr": 1, "sra": 2}   # sra: SR at accumulation points only
 STATUS_OVERFLOW, STATUS_MAX_EVENTS, STATUS_STATE_RANGE, STATUS_NAN = 1, 2, 4, 8
 SSA_OK, SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_ETIMEDOUT = 0, -1, -2, -3, -4
 FAMILIES = {0: "general", 1: "birth_death", 2: "schlogl", 3: "telegraph", 4: "dimer", 5: "repressilator"}

@@ -72,7 +72,7 @@ def test_model_create_rejects(ssa, bad):
     assert e.value.code == ssa.SSA_EINVAL
 
 
-@pytest.mark.parametrize("case", ["precision", "sr_fp64", "t_end", "unsorted", "beyond", "no_samples", "state_bytes",
+@pytest.mark.parametrize("case", ["precision", "sr_fp64", "sra_mixed", "t_end", "unsorted", "beyond", "no_samples", "state_bytes",
                                   "max_events", "ids", "x0"])
 def test_run_rejects_before_launch(ssa, case):
     m = ssa.Model.from_dict(P.birth_death())
@@ -82,6 +82,8 @@ def test_run_rejects_before_launch(ssa, case):
         kw["precision"] = 9
     elif case == "sr_fp64":
         kw["precision"], kw["rounding"] = "fp64", "sr"
+    elif case == "sra_mixed":
+        kw["precision"], kw["rounding"] = "mixed_f16", "sra"
     elif case == "t_end":
         kw["t_end"] = 0.0
     elif case == "unsorted":

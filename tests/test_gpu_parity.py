@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 MODES = [("fp64", "rn"), ("fp32", "rn"), ("mixed_f16", "rn"), ("mixed_f16", "sr"), ("mixed_bf16", "rn"),
          ("mixed_bf16", "sr"), ("uniform_f16", "rn"), ("uniform_f16", "sr"), ("uniform_bf16", "rn"),
-         ("uniform_bf16", "sr")]
+         ("uniform_bf16", "sr"), ("uniform_f16", "sra"), ("uniform_bf16", "sra")]
 
 
 @pytest.fixture(scope="module")

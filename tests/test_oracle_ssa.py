@@ -310,3 +310,28 @@ def test_trajectories_depend_only_on_global_id():
     part = oracle.run(m, P.TELEGRAPH_X0, 32, 10.0, [5.0, 10.0], "uniform_f16", "sr", seed=9, g0=32)
     np.testing.assert_array_equal(whole["snapshots"][:, :, 32:], part["snapshots"])
     np.testing.assert_array_equal(whole["t_final"][32:], part["t_final"])
+
+
+def test_selective_sr_recovers_the_underflow_failure():
+    """Sec. 3.3 names selective SR (SR only at accumulation points) without
+    testing it: with the partial sums and the clock rounded stochastically and
+    everything else to nearest, uniform BF16 no longer swamps kon = 0.01."""
+    m = P.telegraph(0.01, 0.1, 5.0, 1.0)
+    n = 16000
+    ref = oracle.run_parallel(m, P.TELEGRAPH_X0, n, 200.0, [200.0], precision="fp64", seed=101)["snapshots"][-1, 2]
+    sra = oracle.run_parallel(m, P.TELEGRAPH_X0, n, 200.0, [200.0], precision="uniform_bf16", rounding="sra",
+                              seed=404, max_events=100000)["snapshots"][-1, 2]
+    assert stats.ks_2samp(ref, sra)[1] > 0.01 and abs(sra.mean() - ref.mean()) < 0.05
+
+
+def test_selective_sr_rounds_only_accumulations():
+    """Selective SR differs from RN only through the sums and the clock: with
+    the clock kept exact (t_end tiny and dyadic rates), and one reaction, the
+    partial sums do not exist and the two runs agree step for step."""
+    m = {"order": np.array([[1]]), "stoich": np.array([[-1]]), "rate": np.array([1.0]), "law": np.array([0])}
+    a = oracle.run(m, [40], 500, 0.25, [0.125, 0.25], "uniform_f16", "rn", seed=3)
+    b = oracle.run(m, [40], 500, 0.25, [0.125, 0.25], "uniform_f16", "sra", seed=3)
+    # same draws and RN propensities; only t_new's rounding may differ
+    assert np.mean(np.all(a["snapshots"] == b["snapshots"], axis=(0, 1))) > 0.5
+    with pytest.raises(ValueError):
+        oracle.run(m, [40], 10, 1.0, [1.0], "mixed_f16", "sra", seed=3)

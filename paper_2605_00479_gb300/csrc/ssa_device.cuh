@@ -46,6 +46,12 @@ constexpr int kMaxN = 8;
 constexpr int kMaxM = 16;
 constexpr int kMaxK = 1024;
 
+// Minimum resident 256-thread blocks per SM requested from the register
+// allocator for the single-model kernels (1 = no register cap below 255).
+#ifndef SSA_MIN_BLOCKS
+#define SSA_MIN_BLOCKS 1
+#endif
+
 enum Precision { FP64 = 0, FP32 = 1, MIXED_F16 = 2, MIXED_BF16 = 3, UNIFORM_F16 = 4, UNIFORM_BF16 = 5 };
 enum TrajStatus { ST_OVERFLOW = 1, ST_MAX_EVENTS = 2, ST_STATE_RANGE = 4, ST_NAN = 8 };
 
@@ -906,7 +912,7 @@ __device__ __forceinline__ void load_samples(const double *samples, int K, typen
 // ------------------------------------------------------------- the kernels
 // One model, one queue: arguments in parameter space.
 template <class Model, int PREC, int SR>
-__global__ void __launch_bounds__(256) ssa_kernel(const __grid_constant__ RunArgs a)
+__global__ void __launch_bounds__(256, SSA_MIN_BLOCKS) ssa_kernel(const __grid_constant__ RunArgs a)
 {
     using P = typename ModeTraits<PREC>::P;
     __shared__ P smp[kMaxK];

@@ -173,3 +173,71 @@ def run_parallel(model, x0, n_traj, t_end, sample_times, workers=None, **kw):
         "n_events": np.concatenate([p["n_events"] for p in parts]),
         "t_final": np.concatenate([p["t_final"] for p in parts]),
     }
+
+
+# ------------------------------------------------------------ tau-leaping
+def _tau_lib():
+    L = lib()
+    if not getattr(L, "_tau_ready", False):
+        P = ctypes.c_void_p
+        L.oracle_tau_run.restype = ctypes.c_int
+        L.oracle_tau_run.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P, ctypes.c_int64, ctypes.c_uint64,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_uint64, ctypes.c_int, P, P, P, P]
+        L.oracle_poisson_array.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, P]
+        L.oracle_exp_f32_array.argtypes = [P, ctypes.c_int64, P]
+        L.oracle_exp_f64_array.argtypes = [P, ctypes.c_int64, P]
+        L._tau_ready = True
+    return L
+
+
+def exp_f32(x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.zeros(x.shape, dtype=np.float32)
+    _tau_lib().oracle_exp_f32_array(_p(x), x.size, _p(out))
+    return out
+
+
+def exp_f64(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(x.shape, dtype=np.float64)
+    _tau_lib().oracle_exp_f64_array(_p(x), x.size, _p(out))
+    return out
+
+
+def poisson(lam, n, prec64=False, seed=0):
+    """n variates of the oracle's Poisson sampler (binary32 or binary64)."""
+    out = np.zeros(n, dtype=np.int64)
+    _tau_lib().oracle_poisson_array(float(lam), int(bool(prec64)), int(seed), int(n), _p(out))
+    return out
+
+
+def tau_run(model, x0, n_traj, t_end, tau, sample_times, precision="fp64", rounding="rn", normalise=False, seed=0,
+            state_bytes=4, g0=0):
+    """Tau-leaping trajectories (fixed leap tau) on the oracle; same outputs as ``run``
+    (n_events = reactions fired, t_final = end of the last leap)."""
+    order = np.ascontiguousarray(model["order"], dtype=np.int32)
+    M, N = order.shape
+    stoich = np.ascontiguousarray(model["stoich"], dtype=np.int32)
+    rate = np.ascontiguousarray(model["rate"], dtype=np.float64)
+    law = np.ascontiguousarray(model.get("law", np.zeros(M)), dtype=np.int32)
+    hill = model.get("hill")
+    hill = None if hill is None else np.ascontiguousarray(hill, dtype=np.float64).reshape(M, 4)
+    const = model.get("constant")
+    const = None if const is None else np.ascontiguousarray(const, dtype=np.uint8)
+    x0 = np.ascontiguousarray(x0, dtype=np.int32)
+    st = np.ascontiguousarray(sample_times, dtype=np.float64)
+    K = st.size
+    out = np.zeros((K, N, n_traj), dtype=np.int16 if state_bytes == 2 else np.int32)
+    status = np.zeros(n_traj, dtype=np.uint32)
+    nev = np.zeros(n_traj, dtype=np.int64)
+    tf = np.zeros(n_traj, dtype=np.float64)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    rnd = ROUNDINGS[rounding] if isinstance(rounding, str) else int(rounding)
+    rc = _tau_lib().oracle_tau_run(N, M, _p(order), _p(stoich), _p(rate), _p(law), _p(hill), _p(const), _p(x0),
+                                   int(n_traj), int(g0), float(t_end), float(tau), K, _p(st), prec, rnd,
+                                   int(bool(normalise)), int(seed) & 0xFFFFFFFFFFFFFFFF, int(state_bytes),
+                                   _p(out), _p(status), _p(nev), _p(tf))
+    if rc != 0:
+        raise ValueError("oracle_tau_run rejected its arguments")
+    return {"snapshots": out, "status": status, "n_events": nev, "t_final": tf}

@@ -89,6 +89,7 @@
 #include <stdint.h>
 #include <string.h>
 #include <stdlib.h>
+#include <math.h>   /* sqrt, sqrtf, floor, floorf, ceil (IEEE, exact) */
 
 /* ------------------------------------------------------------------------ */
 /* Bit access                                                                */
@@ -790,4 +791,382 @@ void oracle_philox_array(const uint32_t ctr[4], const uint32_t key[2], int64_t n
         c[0] = ctr[0] + (uint32_t)i; c[1] = ctr[1]; c[2] = ctr[2]; c[3] = ctr[3];
         oracle_philox4x32_10(c, key, out + 4 * i);
     }
+}
+
+/* ======================================================================== */
+/* Mixed-precision tau-leaping (the paper names the combination of reduced  */
+/* precision with tau-leaping as future work, Sec. 5 and Sec. 6; explicit    */
+/* tau-leaping is the approximate method of its Table "taxonomy").           */
+/*                                                                           */
+/* Readings:                                                                 */
+/*  T1 fixed leap size tau; leap n covers [n tau, (n+1) tau); L =            */
+/*     ceil(t_end / tau) leaps; the leap grid is exact (binary64), precision */
+/*     applies to propensities, lambda and the Poisson sampler.              */
+/*  T2 a_j by reading R3 (RN/SR per mode; SR slots from stream 1, leap n     */
+/*     owning blocks [nB, (n+1)B)); lambda_j = a_j tau in the accumulator    */
+/*     type (binary64 / binary32), or rnd16(a_j * rnd16(tau)) in uniform     */
+/*     mode (one SR slot per channel, after the chains).                     */
+/*  T3 k_j ~ Poisson(lambda_j) by the sampler below in binary64 (FP64 mode)  */
+/*     or binary32 (all other modes); its uniforms come from Philox with     */
+/*     counter = (word block, leap n, trajectory id, 2 + j).                 */
+/*  T4 x += sum_j nu_j k_j in 64-bit integers; a negative count is set to 0  */
+/*     and flagged TAU_CLAMPED (16); events += sum_j k_j.                    */
+/*  T5 snapshots: before leap n, every s_k < (n+1) tau receives the current  */
+/*     state; after the last leap the remaining ones receive the final one. */
+/* ======================================================================== */
+enum { ST_TAU_CLAMPED = 16 };
+
+/* exp by Cody-Waite reduction x = k ln2 + r, |r| <= ln2/2, Taylor series of  */
+/* e^r (to r^7 in binary32, r^13 in binary64), scaled by 2^k.  Domain        */
+/* [-30, 0] (the sampler needs exp(-lambda) for lambda < 10).               */
+float oracle_exp_f32(float x)
+{
+    const float LN2_HI = 0x1.62e400p-1f;
+    const float LN2_LO = 0x1.7f7d1cp-20f;
+    const float INV_LN2 = 0x1.715476p+0f;
+    float kf = x * INV_LN2;
+    kf = kf + 0.5f;
+    int k = (int)kf;
+    if ((float)k > kf) k -= 1;                         /* floor */
+    float fk = (float)k;
+    float r = x - fk * LN2_HI;
+    r = r - fk * LN2_LO;
+    float p = 1.0f / 5040.0f;
+    p = p * r + 1.0f / 720.0f;
+    p = p * r + 1.0f / 120.0f;
+    p = p * r + 1.0f / 24.0f;
+    p = p * r + 1.0f / 6.0f;
+    p = p * r + 0.5f;
+    p = p * r + 1.0f;
+    p = p * r + 1.0f;
+    return p * u2f((uint32_t)(k + 127) << 23);
+}
+
+double oracle_exp_f64(double x)
+{
+    const double LN2_HI = 0x1.62e42fee00000p-1;
+    const double LN2_LO = 0x1.a39ef35793c76p-33;
+    const double INV_LN2 = 0x1.71547652b82fep+0;
+    double kf = x * INV_LN2;
+    kf = kf + 0.5;
+    int k = (int)kf;
+    if ((double)k > kf) k -= 1;
+    double fk = (double)k;
+    double r = x - fk * LN2_HI;
+    r = r - fk * LN2_LO;
+    double p = 1.0 / 6227020800.0;                     /* 1/13! */
+    p = p * r + 1.0 / 479001600.0;
+    p = p * r + 1.0 / 39916800.0;
+    p = p * r + 1.0 / 3628800.0;
+    p = p * r + 1.0 / 362880.0;
+    p = p * r + 1.0 / 40320.0;
+    p = p * r + 1.0 / 5040.0;
+    p = p * r + 1.0 / 720.0;
+    p = p * r + 1.0 / 120.0;
+    p = p * r + 1.0 / 24.0;
+    p = p * r + 1.0 / 6.0;
+    p = p * r + 0.5;
+    p = p * r + 1.0;
+    p = p * r + 1.0;
+    return p * u2d((uint64_t)(k + 1023) << 52);
+}
+
+/* log k! : summed logarithms below 10, Stirling's series above. */
+static float logfact_f32(float k)
+{
+    if (k < 10.0f) {
+        float s = 0.0f;
+        for (int i = 2; (float)i <= k; ++i) s = s + oracle_log_f32((float)i);
+        return s;
+    }
+    const float HALF_LN_2PI = 0x1.d67f1cp-1f;           /* 0.5 ln(2 pi) */
+    float x = k + 1.0f;
+    float lx = oracle_log_f32(x);
+    float s = (x - 0.5f) * lx;
+    s = s - x;
+    s = s + HALF_LN_2PI;
+    s = s + (1.0f / 12.0f) / x;
+    s = s - (1.0f / 360.0f) / (x * x * x);
+    return s;
+}
+
+static double logfact_f64(double k)
+{
+    if (k < 10.0) {
+        double s = 0.0;
+        for (int i = 2; (double)i <= k; ++i) s = s + oracle_log_f64((double)i);
+        return s;
+    }
+    const double HALF_LN_2PI = 0x1.d67f1c864beb5p-1;
+    double x = k + 1.0;
+    double lx = oracle_log_f64(x);
+    double s = (x - 0.5) * lx;
+    s = s - x;
+    s = s + HALF_LN_2PI;
+    s = s + (1.0 / 12.0) / x;
+    s = s - (1.0 / 360.0) / (x * x * x);
+    s = s + (1.0 / 1260.0) / (x * x * x * x * x);
+    return s;
+}
+
+typedef struct {
+    uint32_t key[2];
+    uint32_t leap, traj, stream;
+    uint32_t w;          /* next word */
+    uint32_t buf[4];
+    int have;
+} sampler_words;
+
+static uint32_t sampler_next(sampler_words *s)
+{
+    if ((s->w & 3u) == 0 || !s->have) {
+        uint32_t ctr[4] = {s->w >> 2, s->leap, s->traj, s->stream};
+        oracle_philox4x32_10(ctr, s->key, s->buf);
+        s->have = 1;
+    }
+    return s->buf[s->w++ & 3u];
+}
+
+/* Poisson(lambda) in binary32: multiplication method below 10 (Knuth),     */
+/* transformed rejection (Hoermann 1993, "PTRS") at 10 and above.           */
+static int64_t poisson_f32(float lam, sampler_words *s)
+{
+    if (!(lam > 0.0f)) return 0;
+    if (lam < 10.0f) {
+        const float L = oracle_exp_f32(-lam);
+        float p = 1.0f;
+        int64_t k = -1;
+        for (int it = 0; it < 1000; ++it) {
+            const float v = (float)((sampler_next(s) >> 8) + 1u) * 0x1p-24f;
+            k += 1;
+            p = p * v;
+            if (!(p > L)) return k;
+        }
+        return k;
+    }
+    const float slam = sqrtf(lam);
+    const float loglam = oracle_log_f32(lam);
+    const float b = 0.931f + 2.53f * slam;
+    const float a = -0.059f + 0.02483f * b;
+    const float invalpha = 1.1239f + 1.1328f / (b - 3.4f);
+    const float vr = 0.9277f - 3.6224f / (b - 2.0f);
+    const float log_invalpha = oracle_log_f32(invalpha);
+    const float kmax = lam + 64.0f * slam + 64.0f;
+    for (int it = 0; it < 100; ++it) {
+        const float U = (float)(sampler_next(s) >> 8) * 0x1p-24f - 0.5f;
+        const float V = (float)((sampler_next(s) >> 8) + 1u) * 0x1p-24f;
+        const float aU = U < 0.0f ? -U : U;
+        const float us = 0.5f - aU;
+        if (!(us > 0.0f)) continue;
+        float kf = (2.0f * a / us + b) * U;
+        kf = kf + lam;
+        kf = kf + 0.43f;
+        kf = floorf(kf);
+        if (us >= 0.07f && V <= vr) return (int64_t)kf;
+        if (kf < 0.0f || (us < 0.013f && V > us)) continue;
+        if (kf > kmax) continue;
+        float lhs = oracle_log_f32(V) + log_invalpha;
+        lhs = lhs - oracle_log_f32(a / (us * us) + b);
+        float rhs = -lam + kf * loglam;
+        rhs = rhs - logfact_f32(kf);
+        if (lhs <= rhs) return (int64_t)kf;
+    }
+    return (int64_t)floorf(lam);
+}
+
+static int64_t poisson_f64(double lam, sampler_words *s)
+{
+    if (!(lam > 0.0)) return 0;
+    if (lam < 10.0) {
+        const double L = oracle_exp_f64(-lam);
+        double p = 1.0;
+        int64_t k = -1;
+        for (int it = 0; it < 1000; ++it) {
+            const double v = ((double)sampler_next(s) + 1.0) * 0x1p-32;
+            k += 1;
+            p = p * v;
+            if (!(p > L)) return k;
+        }
+        return k;
+    }
+    const double slam = sqrt(lam);
+    const double loglam = oracle_log_f64(lam);
+    const double b = 0.931 + 2.53 * slam;
+    const double a = -0.059 + 0.02483 * b;
+    const double invalpha = 1.1239 + 1.1328 / (b - 3.4);
+    const double vr = 0.9277 - 3.6224 / (b - 2.0);
+    const double log_invalpha = oracle_log_f64(invalpha);
+    const double kmax = lam + 64.0 * slam + 64.0;
+    for (int it = 0; it < 100; ++it) {
+        const double U = (double)sampler_next(s) * 0x1p-32 - 0.5;
+        const double V = ((double)sampler_next(s) + 1.0) * 0x1p-32;
+        const double aU = U < 0.0 ? -U : U;
+        const double us = 0.5 - aU;
+        if (!(us > 0.0)) continue;
+        double kf = (2.0 * a / us + b) * U;
+        kf = kf + lam;
+        kf = kf + 0.43;
+        kf = floor(kf);
+        if (us >= 0.07 && V <= vr) return (int64_t)kf;
+        if (kf < 0.0 || (us < 0.013 && V > us)) continue;
+        if (kf > kmax) continue;
+        double lhs = oracle_log_f64(V) + log_invalpha;
+        lhs = lhs - oracle_log_f64(a / (us * us) + b);
+        double rhs = -lam + kf * loglam;
+        rhs = rhs - logfact_f64(kf);
+        if (lhs <= rhs) return (int64_t)kf;
+    }
+    return (int64_t)floor(lam);
+}
+
+/* one tau-leaping trajectory; prec as in oracle_run, sr 0/1 */
+static void tau_traj(const omodel *md, int prec, int sr, double t_end, double tau, int K, const double *samples,
+                     uint64_t seed, uint32_t traj, int32_t *x, const sink *S, uint32_t *status, int64_t *n_events,
+                     double *t_final)
+{
+    const int M = md->M, N = md->N;
+    const int fmt = (prec == P_MIXED_BF16 || prec == P_UNIFORM_BF16) ? 1 : 0;
+    const int is16 = prec >= P_MIXED_F16, uniform = prec >= P_UNIFORM_F16;
+    double cp64[OR_MAX_M], h064[OR_MAX_M], h164[OR_MAX_M];
+    float cp[OR_MAX_M], h0[OR_MAX_M], h1[OR_MAX_M], a[OR_MAX_M];
+    int nsr = 0;
+    for (int j = 0; j < M; ++j) {
+        cp64[j] = md->cprime[j];
+        h064[j] = md->law[j] == LAW_HILL ? md->hill[4 * j] : 0.0;
+        h164[j] = md->law[j] == LAW_HILL ? md->hill[4 * j + 1] : 0.0;
+        cp[j] = (float)cp64[j];
+        h0[j] = (float)h064[j];
+        h1[j] = (float)h164[j];
+        if (is16) { cp[j] = rn16(fmt, cp[j]); h0[j] = rn16(fmt, h0[j]); h1[j] = rn16(fmt, h1[j]); }
+        nsr += chain_ops(md, j);
+    }
+    if (uniform) nsr += M;
+    const uint64_t Ws = 4u * (uint64_t)((nsr + 7) / 8);
+    const float tau32 = (float)tau;
+    const float tau16 = is16 ? rn16(fmt, tau32) : tau32;
+    word_stream wsr;
+    memset(&wsr, 0, sizeof(wsr));
+    wsr.key[0] = (uint32_t)seed; wsr.key[1] = (uint32_t)(seed >> 32); wsr.traj = traj; wsr.stream = 1;
+    rounder R;
+    R.bf16 = fmt; R.sr = sr; R.ws = &wsr; R.sr_base = 0; R.op = 0;
+    const int64_t L = (int64_t)ceil(t_end / tau);
+    int k = 0;
+    int64_t events = 0;
+    double t_last = 0.0;
+    for (int64_t n = 0; n < L; ++n) {
+        const double t_next = (double)(n + 1) * tau;
+        while (k < K && samples[k] < t_next) write_snapshot(S, k++, x, status);
+        double lam64[OR_MAX_M];
+        float lam32[OR_MAX_M];
+        R.sr_base = (uint64_t)n * Ws;
+        R.op = 0;
+        int bad = 0;
+        for (int j = 0; j < M; ++j) {
+            if (prec == P_FP64) {
+                lam64[j] = prop_f64(md, j, x, cp64, h064, h164) * tau;
+                if (f64_is_nan(lam64[j])) bad |= ST_NAN; else if (f64_is_inf(lam64[j])) bad |= ST_OVERFLOW;
+            } else {
+                a[j] = is16 ? prop_16(md, j, x, cp, h0, h1, &R) : prop_f32(md, j, x, cp, h0, h1);
+            }
+        }
+        if (prec != P_FP64) {
+            for (int j = 0; j < M; ++j) {
+                lam32[j] = uniform ? rnd16(&R, a[j] * tau16) : a[j] * tau32;
+                if (f32_is_nan(lam32[j])) bad |= ST_NAN; else if (f32_is_inf(lam32[j])) bad |= ST_OVERFLOW;
+            }
+        }
+        if (bad) { *status |= (uint32_t)bad; break; }
+        int64_t dx[OR_MAX_N];
+        for (int i = 0; i < N; ++i) dx[i] = 0;
+        for (int j = 0; j < M; ++j) {
+            sampler_words sw;
+            memset(&sw, 0, sizeof(sw));
+            sw.key[0] = (uint32_t)seed; sw.key[1] = (uint32_t)(seed >> 32);
+            sw.leap = (uint32_t)n; sw.traj = traj; sw.stream = 2u + (uint32_t)j;
+            const int64_t kj = prec == P_FP64 ? poisson_f64(lam64[j], &sw) : poisson_f32(lam32[j], &sw);
+            events += kj;
+            for (int i = 0; i < N; ++i)
+                if (!(md->constant && md->constant[i])) dx[i] += kj * (int64_t)md->stoich[j * N + i];
+        }
+        for (int i = 0; i < N; ++i) {
+            int64_t v = (int64_t)x[i] + dx[i];
+            if (v < 0) { v = 0; *status |= ST_TAU_CLAMPED; }
+            if (v > 2147483647) v = 2147483647;
+            x[i] = (int32_t)v;
+        }
+        t_last = t_next;
+    }
+    while (k < K) write_snapshot(S, k++, x, status);
+    *n_events = events;
+    *t_final = t_last;
+}
+
+int oracle_tau_run(int N, int M, const int32_t *order, const int32_t *stoich, const double *rate,
+                   const int32_t *law, const double *hill, const uint8_t *constant,
+                   const int32_t *x0, int64_t n_traj, uint64_t g0, double t_end, double tau,
+                   int K, const double *samples, int precision, int rounding, int normalise,
+                   uint64_t seed, int state_bytes, void *out, uint32_t *status, int64_t *n_events, double *t_final)
+{
+    if (N < 1 || N > OR_MAX_N || M < 1 || M > OR_MAX_M || K < 0 || K > 1024) return -1;
+    if (precision < 0 || precision > 5 || rounding < 0 || rounding > 1) return -1;
+    if (rounding == 1 && precision < 2) return -1;
+    if (!(tau > 0.0) || !(t_end > 0.0) || t_end / tau > 2147483647.0) return -1;
+    if (state_bytes != 2 && state_bytes != 4) return -1;
+    if (n_traj < 0 || g0 + (uint64_t)n_traj > 0x100000000ull) return -1;
+    omodel md;
+    memset(&md, 0, sizeof(md));
+    md.N = N; md.M = M; md.order = order; md.stoich = stoich; md.law = law;
+    md.hill = hill; md.constant = constant; md.normalise = normalise;
+    for (int j = 0; j < M; ++j) {
+        if (law[j] == LAW_HILL) { md.cprime[j] = 0.0; continue; }
+        double denom = 1.0;
+        for (int i = 0; i < N; ++i) denom = denom * factorial(order[j * N + i]);
+        double c = rate[j] / denom;
+        if (normalise && constant) {
+            for (int i = 0; i < N; ++i) {
+                if (!constant[i] || order[j * N + i] == 0) continue;
+                for (int m = 0; m < order[j * N + i]; ++m) c = c * (double)(x0[i] - m);
+                md.folded[j][i] = 1;
+            }
+        }
+        md.cprime[j] = c;
+    }
+    for (int64_t r = 0; r < n_traj; ++r) {
+        int32_t x[OR_MAX_N];
+        for (int i = 0; i < N; ++i) x[i] = x0[i];
+        sink S;
+        S.out = out; S.state_bytes = state_bytes; S.n_traj = n_traj; S.col = r; S.K = K; S.N = N;
+        uint32_t st = 0;
+        int64_t ne = 0;
+        double tf = 0.0;
+        tau_traj(&md, precision, rounding, t_end, tau, K, samples, seed, (uint32_t)(g0 + (uint64_t)r), x, &S, &st,
+                 &ne, &tf);
+        if (status) status[r] = st;
+        if (n_events) n_events[r] = ne;
+        if (t_final) t_final[r] = tf;
+    }
+    return 0;
+}
+
+/* Sampler checks: n Poisson(lambda) variates from (leap, traj, stream) word */
+/* sequences leap = i, traj = 0, stream = 2; prec64 selects binary64.       */
+void oracle_poisson_array(double lam, int prec64, uint64_t seed, int64_t n, int64_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        sampler_words sw;
+        memset(&sw, 0, sizeof(sw));
+        sw.key[0] = (uint32_t)seed; sw.key[1] = (uint32_t)(seed >> 32);
+        sw.leap = (uint32_t)i; sw.traj = 0; sw.stream = 2;
+        out[i] = prec64 ? poisson_f64(lam, &sw) : poisson_f32((float)lam, &sw);
+    }
+}
+
+void oracle_exp_f32_array(const float *x, int64_t n, float *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_exp_f32(x[i]);
+}
+
+void oracle_exp_f64_array(const double *x, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_exp_f64(x[i]);
 }

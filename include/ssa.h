@@ -79,7 +79,8 @@ enum {
     SSA_TRAJ_OVERFLOW = 1,     /* a0 = +inf: the trajectory stops at its current state */
     SSA_TRAJ_MAX_EVENTS = 2,   /* the event cap was reached before t_end */
     SSA_TRAJ_STATE_RANGE = 4,  /* a count went negative, or did not fit int16 storage */
-    SSA_TRAJ_NAN = 8           /* a0 = NaN */
+    SSA_TRAJ_NAN = 8,          /* a0 = NaN */
+    SSA_TRAJ_TAU_CLAMPED = 16  /* tau-leaping: a leap drove a count below 0; it was set to 0 */
 };
 
 /* Limits of this build. */
@@ -160,6 +161,43 @@ int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_
                           int precision, int rounding, int normalise, uint64_t seed,
                           int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
                           int64_t *n_events, double *t_final, void *stream);
+
+/*
+ * ssa_tau_run -- explicit tau-leaping with a fixed leap (the approximate
+ * methods of Sec. 1 and Sec. 2, run in the reduced-precision modes; Sec. 5
+ * lists this interaction as untested and Sec. 6 as future work).  Leap n covers
+ * [n tau, (n+1) tau), n = 0 .. ceil(t_end / tau) - 1; in each leap every
+ * reaction j fires k_j ~ Poisson(a_j(x) tau) times at once and
+ * x += sum_j nu_j k_j.
+ *   a_j           the direct method's propensity arithmetic (same rounding
+ *                 chain, same SR operation indices 0 .. S-1 per leap)
+ *   lambda_j      a_j * tau in binary64 (SSA_FP64), binary32 (SSA_FP32 and
+ *                 mixed modes), or in uniform modes rnd16(a_j * rnd16(tau))
+ *                 with SR operation index S + j
+ *   k_j           Poisson sampler in binary64 (SSA_FP64) or binary32:
+ *                 multiplication method below lambda = 10, Hoermann's
+ *                 transformed rejection (PTRS) from 10; its uniforms come from
+ *                 Philox4x32-10 with counter (word / 4, n, trajectory id, 2 + j)
+ *   counts        updated in 64-bit integers; a count that would go negative
+ *                 is set to 0 and flagged SSA_TRAJ_TAU_CLAMPED; counts are
+ *                 capped at 2^31 - 1
+ * Arguments as ssa_ensemble_run, except:
+ *   tau           leap length, finite, > 0, t_end / tau <= 2^31 - 1
+ *   rounding      SSA_RN or SSA_SR (SSA_SR_ACCUM is rejected)
+ *   sample_times  snapshot k holds the state after every leap that ends at
+ *                 or before s_k (leaps end at (n+1) tau)
+ *   n_events      device [n_traj] total reactions fired (sum of the k_j), or NULL
+ *   t_final       device [n_traj] end time of the last completed leap, or NULL
+ * A propensity that evaluates to +inf or NaN stops the trajectory at the
+ * start of that leap with SSA_TRAJ_OVERFLOW or SSA_TRAJ_NAN.  The model may
+ * use any structure (the general table-driven kernel serves every model).
+ * Allocates an 8-byte work-queue counter as ssa_ensemble_run does.
+ * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA.
+ */
+int ssa_tau_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, const int32_t *x0,
+                double t_end, double tau, int n_samples, const double *sample_times, int precision,
+                int rounding, int normalise, uint64_t seed, int state_bytes, void *out,
+                uint32_t *traj_status, int64_t *n_events, double *t_final, void *stream);
 
 /*
  * ssa_set_launch_config -- launch shape for subsequent runs in this process.
@@ -284,8 +322,8 @@ int ssa_sweep_run_noalloc(const ssa_model *model, int64_t n_sets, int64_t traj_p
                           int64_t *n_events, double *t_final, void *stream);
 
 /*
- * Learned surrogate for the telegraph model (a spec extension; the
- * paper trains no network).  A multilayer perceptron maps 4 standardised
+ * Learned surrogate for the telegraph model (an extension beyond the paper; it
+ * trains no network).  A multilayer perceptron maps 4 standardised
  * log-parameters (log kon, log koff, log km, log gamma) through three hidden
  * layers of 256 GELU units to a 128-bin softmax over the mRNA count (bins
  * 0..127, the last holding >= 127).  bf16 weights and activations, fp32

@@ -364,6 +364,68 @@ int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_
     return rc;
 }
 
+
+int ssa_tau_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, const int32_t *x0, double t_end,
+                double tau, int n_samples, const double *sample_times, int precision, int rounding, int normalise,
+                uint64_t seed, int state_bytes, void *out, uint32_t *traj_status, int64_t *n_events,
+                double *t_final, void *stream)
+{
+    int rc = validate_run(model, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding, 0,
+                          state_bytes);
+    if (rc != SSA_OK) return rc;
+    if (rounding == SSA_SR_ACCUM) return fail(SSA_EINVAL, "tau-leaping supports SSA_RN and SSA_SR only");
+    if (!finite_double(tau) || !(tau > 0.0)) return fail(SSA_EINVAL, "tau must be finite and > 0");
+    if (!(t_end / tau <= 2147483647.0)) return fail(SSA_EINVAL, "t_end / tau must be <= 2^31 - 1");
+    if (n_traj > 0 && (!out || !traj_status)) return fail(SSA_EINVAL, "out and traj_status are required");
+    if (n_traj == 0) return SSA_OK;
+
+    ssa::RunArgs *a = new (std::nothrow) ssa::RunArgs;
+    if (!a) return fail(SSA_ENOMEM, "out of host memory");
+    std::memset(a, 0, sizeof(*a));
+    fill_structure(*model, normalise, x0, *a);
+    a->K = n_samples;
+    a->n_traj = n_traj;
+    a->n_work = n_traj;
+    a->slice_pairs = 1;
+    a->traj_offset = (uint32_t)traj_offset;
+    a->n_sets = 1;
+    a->traj_per_set = n_traj;
+    a->t_end = t_end;
+    a->tau = tau;
+    a->n_leaps = (int64_t)std::ceil(t_end / tau);
+    for (int k = 0; k < n_samples; ++k) a->samples[k] = sample_times[k];
+    a->key0 = (uint32_t)seed;
+    a->key1 = (uint32_t)(seed >> 32);
+    a->out = out;
+    a->state_bytes = state_bytes;
+    a->status = traj_status;
+    a->n_events = n_events;
+    a->t_final = t_final;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long *head = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&head), sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        delete a;
+        return e == cudaErrorMemoryAllocation ? fail(SSA_ENOMEM, "work-queue counter: out of device memory")
+                                              : cuda_fail(e, "cudaMallocAsync");
+    }
+    e = cudaMemsetAsync(head, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(head, s);
+        delete a;
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    a->queue_head = head;
+    int grid = 0;
+    e = ssa::launch_tau(*a, precision, rounding, g_cfg, s, &grid);
+    cudaError_t e2 = cudaFreeAsync(head, s);
+    delete a;
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return SSA_OK;
+}
+
 }  // extern "C"
 
 // ======================================================================

@@ -84,6 +84,8 @@ struct RunArgs {
     const double *hill_tab;            // [n_sets][M][2] (alpha0, alpha) or null
     const int32_t *x0_tab;             // [n_sets][N] or null (then x0 above)
     double t_end;
+    double tau;                        // tau-leaping: leap size (0 for the direct method)
+    int64_t n_leaps;                   // tau-leaping: ceil(t_end / tau)
     double samples[kMaxK];
     uint32_t key0, key1;
     int64_t max_events;
@@ -419,7 +421,8 @@ struct Lane {
     uint16_t c16[Model::M], h016[Model::M], h116[Model::M];   // bit patterns (RN 16-bit modes)
     P t;
     P s_next;            // next sample time (or +inf)
-    int64_t n;           // events fired
+    int64_t n;           // events fired (direct method) / leaps done (tau-leaping)
+    int64_t ev;          // reactions fired (tau-leaping)
     int64_t item;        // work item
     uint32_t traj;       // global trajectory id
     int k;               // next snapshot
@@ -730,6 +733,40 @@ __device__ __forceinline__ void ssa_step(const RunArgs &a, Lane<Model, PREC> &L,
     }
 }
 
+// Propensities of the general model (runtime structure), reading R3.
+template <int PREC, int SR>
+__device__ __forceinline__ void general_propensities(const RunArgs &a, const Lane<GeneralModel, PREC> &L,
+                                                     Rounder<PREC, SR> &R, typename ModeTraits<PREC>::P *prop)
+{
+    using P = typename ModeTraits<PREC>::P;
+#pragma unroll 1
+    for (int j = 0; j < a.M; ++j) {
+        int op = a.chain_start[j];
+        if (a.law[j] == 1) {
+            const P Pv = R.rnd((P)L.x[a.hill_reg[j]], op++);
+            P q = Pv;
+            for (int m = 1; m < a.hill_h[j]; ++m) q = R.rnd(q * Pv, op++);
+            const P d = R.rnd(P(1) + q, op++);
+            const P f = R.rnd(L.h1[j] / d, op++);
+            prop[j] = R.rnd(L.h0[j] + f, op++);
+        } else {
+            P av = L.c[j];
+            bool zero = false;
+#pragma unroll 1
+            for (int i = 0; i < a.N; ++i) {
+                const int r = a.order[j][i];
+                if (r == 0 || a.folded[j][i]) continue;
+                zero = zero || (L.x[i] < r);
+                for (int m = 0; m < r; ++m) {
+                    const P f = R.rnd((P)(L.x[i] - m), op++);
+                    av = R.rnd(av * f, op++);
+                }
+            }
+            prop[j] = zero ? P(0) : av;
+        }
+    }
+}
+
 // ------------------------------------------------- one step, general model
 // Same contract as ssa_step, with the structure read from the kernel
 // arguments in runtime loops (state and tables in local memory).  Used for
@@ -760,32 +797,7 @@ __device__ __noinline__ void ssa_step_general(const RunArgs &a, Lane<GeneralMode
 
     // propensities
     P prop[kMaxM];
-#pragma unroll 1
-    for (int j = 0; j < a.M; ++j) {
-        int op = a.chain_start[j];
-        if (a.law[j] == 1) {
-            const P Pv = R.rnd((P)L.x[a.hill_reg[j]], op++);
-            P q = Pv;
-            for (int m = 1; m < a.hill_h[j]; ++m) q = R.rnd(q * Pv, op++);
-            const P d = R.rnd(P(1) + q, op++);
-            const P f = R.rnd(L.h1[j] / d, op++);
-            prop[j] = R.rnd(L.h0[j] + f, op++);
-        } else {
-            P av = L.c[j];
-            bool zero = false;
-#pragma unroll 1
-            for (int i = 0; i < a.N; ++i) {
-                const int r = a.order[j][i];
-                if (r == 0 || a.folded[j][i]) continue;
-                zero = zero || (L.x[i] < r);
-                for (int m = 0; m < r; ++m) {
-                    const P f = R.rnd((P)(L.x[i] - m), op++);
-                    av = R.rnd(av * f, op++);
-                }
-            }
-            prop[j] = zero ? P(0) : av;
-        }
-    }
+    general_propensities<PREC, SR>(a, L, R, prop);
     // partial sums
     P S[kMaxM];
     S[0] = prop[0];

@@ -27,6 +27,10 @@ cudaError_t launch_telegraph(const RunArgs &, int, int, int, LaunchConfig, cudaS
 cudaError_t launch_dimer(const RunArgs &, int, int, int, LaunchConfig, cudaStream_t, int *);
 cudaError_t launch_repressilator(const RunArgs &, int, int, int, LaunchConfig, cudaStream_t, int *);
 
+// Tau-leaping kernel (ssa_k_tau.cu): precision `prec`, rounding `sr` (0 RN,
+// 1 SR), leap a.tau, a.n_leaps leaps.
+cudaError_t launch_tau(const RunArgs &a, int prec, int sr, LaunchConfig cfg, cudaStream_t stream, int *grid_out);
+
 // Shared launch logic: choose the kernel for (prec, sr), size the grid from
 // occupancy (persistent: enough lanes to fill the GPU, no more than the work).
 template <class ModelF>

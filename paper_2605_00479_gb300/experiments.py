@@ -4,6 +4,8 @@
     python -m paper_2605_00479_gb300.experiments scale  [n_traj=1000000] [t_end=1000] [fp64_traj=20000]
     python -m paper_2605_00479_gb300.experiments tables [scale=1]
     python -m paper_2605_00479_gb300.experiments sweeps
+    python -m paper_2605_00479_gb300.experiments dwell
+    python -m paper_2605_00479_gb300.experiments tau    [n_traj=200000]
 
 batch: telegraph (kon, koff log-uniform in [0.05, 5], km in [5, 100], gamma 1),
   dimerisation (k1, k2 log-uniform in [x0.5, x2] around 1e-3, 0.1; M0 = 300)
@@ -26,6 +28,19 @@ tables: the paper's per-model comparisons (Sec. 4.1-4.5 tables): every precision
 sweeps: the telegraph kon sweep (kon in [1e-3, 1e-1], koff = 0.1, alpha = 5,
   beta = 1; uniform modes; W1 to fp64) and the repressilator horizon sweep
   (t_end in {100, 200, 400, 800}; uniform modes; W1 and KS p to fp64).
+dwell: OFF-state dwell times of the bimodal telegraph set (kon = koff = 0.05,
+  alpha = 20, beta = 1): the gene state is sampled at 1024 times to t_end = 200
+  (spacing 0.196, 1% of the mean dwell 20); completed OFF intervals between
+  observed switches are compared with the exponential law of rate kon (mean
+  and KS distance of the sample against the exponential CDF evaluated at the
+  observed, grid-rounded durations) and across precision modes.
+tau: fixed-leap tau-leaping in reduced precision (the combination the paper
+  leaves open): Schloegl (bistable set, normalised, X0 = 250, t_end = 10) and
+  dimerisation (M0 = 300, t_end = 20), leaps tau in {0.02, 0.005, 0.001} and
+  {0.5, 0.1, 0.02}; each mode's X / A at t_end against an fp64 direct-method
+  ensemble (KS p, W1, mean, variance, clamped fraction), and its throughput
+  (trajectories/s, leaps/s, reactions/s) next to the direct method's in mixed
+  fp16.
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -194,11 +209,102 @@ def sweeps(seed=21):
     return out
 
 
+def _off_dwells(goff, dt):
+    """Durations of completed OFF intervals from a [K, n] 0/1 gene-off series."""
+    g = goff.T.astype(np.int8)                        # [n, K]
+    d = np.diff(g, axis=1)                            # +1: switched off, -1: switched on
+    out = []
+    for row in d:
+        starts = np.nonzero(row == 1)[0]
+        ends = np.nonzero(row == -1)[0]
+        j = 0
+        for s0 in starts:
+            while j < len(ends) and ends[j] <= s0:
+                j += 1
+            if j < len(ends):
+                out.append((ends[j] - s0) * dt)
+    return np.array(out)
+
+
+def dwell(n_traj=10000, seed=31):
+    import torch
+    from scipy import stats as sst
+    kon = 0.05
+    md = P.telegraph(kon, 0.05, 20.0, 1.0)
+    m = ssa.Model.from_dict(md)
+    K, t_end = 1024, 200.0
+    samples = P.even_samples(t_end, K)
+    dt = float(samples[1] - samples[0])
+    out = {"kon": kon, "dt": dt, "n_traj": n_traj, "modes": {}}
+    ref = None
+    for prec, rnd in [("fp64", "rn"), ("uniform_bf16", "sr"), ("uniform_bf16", "sra"), ("mixed_f16", "rn"),
+                      ("uniform_bf16", "rn")]:
+        r = ssa.ensemble_run(m, n_traj, P.TELEGRAPH_X0, t_end, samples, prec, rnd, False,
+                             seed if prec == "fp64" else seed + 1, 10**7)
+        torch.cuda.synchronize()
+        d = _off_dwells(r["snapshots"][:, 0, :].cpu().numpy(), dt)
+        row = {"n_dwells": int(d.size)}
+        if d.size:
+            expo = 1.0 - np.exp(-kon * np.sort(d))
+            emp = np.arange(1, d.size + 1) / d.size
+            row.update({"mean": float(d.mean()), "mean_expected": 1.0 / kon,
+                        "ks_vs_exponential": float(np.max(np.abs(emp - expo)))})
+            if ref is None:
+                ref = d
+            else:
+                row["ks_p_vs_fp64"] = float(sst.ks_2samp(ref, d).pvalue)
+                row["w1_vs_fp64"] = float(sst.wasserstein_distance(ref, d))
+        out["modes"][f"{prec}:{rnd}"] = row
+    return out
+
+
+def tau(n_traj=200000, seed=41):
+    import torch
+    cases = [
+        ("schlogl", P.schlogl(), P.schlogl_x0(P.schlogl()), 10.0, True, 0, (0.02, 0.005, 0.001)),
+        ("dimer", P.dimer(), P.dimer_x0(300), 20.0, False, 0, (0.5, 0.1, 0.02)),
+    ]
+    modes = [("fp64", "rn"), ("fp32", "rn"), ("mixed_f16", "rn"), ("uniform_f16", "sr"), ("uniform_bf16", "sr")]
+    out = {"n_traj": n_traj, "note": "x at t_end vs an fp64 direct-method ensemble (different seed)", "models": {}}
+    for name, md, x0, t_end, norm, sp, taus in cases:
+        m = ssa.Model.from_dict(md)
+        ref, _ = _final_states(md, x0, n_traj, t_end, "fp64", "rn", norm, seed, sp)
+        row = {"fp64_ssa": {"mean": float(ref.mean()), "var": float(ref.var())}}
+        res = {}
+
+        def run_ssa():
+            res["r"] = ssa.ensemble_run(m, n_traj, x0, t_end, [t_end], "mixed_f16", "rn", norm, seed + 1, 10**8,
+                                        with_t_final=False)
+        run_ssa()
+        dt = _timed(run_ssa)
+        ev = float(res["r"]["n_events"].double().sum())
+        row["mixed_f16_ssa"] = dict(_compare(ref, res["r"]["snapshots"][0, sp].cpu().numpy()),
+                                    time_s=dt, traj_per_s=n_traj / dt, events_per_s=ev / dt)
+        for tau_ in taus:
+            for prec, rnd in modes:
+                def run_tau():
+                    res["r"] = ssa.tau_run(m, n_traj, x0, t_end, tau_, [t_end], prec, rnd, norm, seed + 2)
+                run_tau()
+                dt = _timed(run_tau)
+                r = res["r"]
+                x = r["snapshots"][0, sp].cpu().numpy()
+                st = r["status"].cpu().numpy()
+                leaps = float(np.ceil(t_end / tau_)) * n_traj
+                d = _compare(ref, x)
+                d.update(time_s=dt, traj_per_s=n_traj / dt, leaps_per_s=leaps / dt,
+                         reactions_per_s=float(r["n_events"].double().sum()) / dt,
+                         clamped=float(np.mean((st & 16) != 0)), stopped=float(np.mean((st & 9) != 0)))
+                row[f"tau={tau_:g}:{prec}:{rnd}"] = d
+        out["models"][name] = row
+        torch.cuda.synchronize()
+    return out
+
+
 if __name__ == "__main__":
     cmd = sys.argv[1]
     kw = {}
     for arg in sys.argv[2:]:
         k, v = arg.split("=")
         kw[k] = float(v) if k in ("t_end", "scale") else int(v)
-    fn = {"batch": batch, "scale": scale, "tables": tables, "sweeps": sweeps}[cmd]
+    fn = {"batch": batch, "scale": scale, "tables": tables, "sweeps": sweeps, "dwell": dwell, "tau": tau}[cmd]
     print(json.dumps(fn(**kw)), flush=True)

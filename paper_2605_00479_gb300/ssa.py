@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libssa_gb300.so")
 
 PRECISION = {"fp64": 0, "fp32": 1, "mixed_f16": 2, "mixed_bf16": 3, "uniform_f16": 4, "uniform_bf16": 5}
 ROUNDING = {"rn": 0, "sr": 1, "sra": 2}   # sra: SR at accumulation points only
-STATUS_OVERFLOW, STATUS_MAX_EVENTS, STATUS_STATE_RANGE, STATUS_NAN = 1, 2, 4, 8
+STATUS_OVERFLOW, STATUS_MAX_EVENTS, STATUS_STATE_RANGE, STATUS_NAN, STATUS_TAU_CLAMPED = 1, 2, 4, 8, 16
 SSA_OK, SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_ETIMEDOUT = 0, -1, -2, -3, -4
 FAMILIES = {0: "general", 1: "birth_death", 2: "schlogl", 3: "telegraph", 4: "dimer", 5: "repressilator"}
 
@@ -31,6 +31,7 @@ SIGNATURES = {
     "ssa_model_kernel_family": (_I, [_P]),
     "ssa_ensemble_run": (_I, _RUN_ARGS),
     "ssa_ensemble_run_host": (_I, _RUN_ARGS),
+    "ssa_tau_run": (_I, [_P, _I64, _U64, _P, _D, _D, _I, _P, _I, _I, _I, _U64, _I, _P, _P, _P, _P, _P]),
     "ssa_set_launch_config": (_I, [_I, _I, _I]),
     "ssa_batch_create": (_I, [_I, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, ctypes.POINTER(_P)]),
     "ssa_batch_launch": (_I, [_P, _P]),
@@ -198,6 +199,33 @@ def ensemble_run_host(model, n_traj, x0, t_end, sample_times, precision="fp64", 
                                        _np_ptr(st), prec, rnd, int(bool(normalise)), int(seed) & (2**64 - 1),
                                        int(max_events), int(state_bytes), _np_ptr(out), _np_ptr(status),
                                        _np_ptr(n_events), _np_ptr(t_final), sp))
+    return {"snapshots": out, "status": status, "n_events": n_events, "t_final": t_final}
+
+
+def tau_run(model, n_traj, x0, t_end, tau, sample_times, precision="fp64", rounding="rn", normalise=False, seed=0,
+            state_bytes=4, out=None, status=None, n_events=None, t_final=None, stream=None, traj_offset=0):
+    """Launch ssa_tau_run (fixed-leap tau-leaping) on CUDA tensors.
+
+    Same outputs as ensemble_run; n_events counts reactions fired and t_final
+    is the end of the last completed leap."""
+    import torch
+    x0, st, prec, rnd = _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision, rounding,
+                                     normalise, seed, 0, state_bytes)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    K = st.size
+    if out is None:
+        out = torch.empty((K, model.N, n_traj), dtype=torch.int16 if state_bytes == 2 else torch.int32, device=dev)
+    if status is None:
+        status = torch.empty(n_traj, dtype=torch.int32, device=dev)
+    if n_events is None:
+        n_events = torch.empty(n_traj, dtype=torch.int64, device=dev)
+    if t_final is None:
+        t_final = torch.empty(n_traj, dtype=torch.float64, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().ssa_tau_run(model.handle, int(n_traj), int(traj_offset), _np_ptr(x0), float(t_end), float(tau), K,
+                             _np_ptr(st), prec, rnd, int(bool(normalise)), int(seed) & (2**64 - 1),
+                             int(state_bytes), _dev_ptr(out), _dev_ptr(status), _dev_ptr(n_events),
+                             _dev_ptr(t_final), ctypes.c_void_p(s.cuda_stream)))
     return {"snapshots": out, "status": status, "n_events": n_events, "t_final": t_final}
 
 

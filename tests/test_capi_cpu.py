@@ -136,3 +136,40 @@ def test_batch_create_rejects_before_allocating(ssa):
     h = ctypes.c_void_p()
     assert L.ssa_batch_create(1, ctypes.cast(arr, ctypes.c_void_p), 10.0, 1, ssa._np_ptr(samples), 2, 0, 0, 0, 1000,
                               4, ctypes.byref(h)) == ssa.SSA_EINVAL
+
+
+@pytest.mark.parametrize("case", ["tau_zero", "tau_nan", "too_many_leaps", "sra", "sr_fp64", "t_end", "state_bytes"])
+def test_tau_run_rejects_before_launch(ssa, case):
+    """ssa_tau_run validates on the host (no device pointer is touched)."""
+    m = ssa.Model.from_dict(P.birth_death())
+    x0 = np.zeros(1, np.int32)
+    st = np.array([0.0, 5.0, 10.0])
+    t_end, tau, prec, rnd, sb = 10.0, 0.1, ssa.PRECISION["fp32"], 0, 4
+    if case == "tau_zero":
+        tau = 0.0
+    elif case == "tau_nan":
+        tau = float("nan")
+    elif case == "too_many_leaps":
+        tau = 1e-9
+    elif case == "sra":
+        prec, rnd = ssa.PRECISION["uniform_f16"], ssa.ROUNDING["sra"]
+    elif case == "sr_fp64":
+        prec, rnd = ssa.PRECISION["fp64"], ssa.ROUNDING["sr"]
+    elif case == "t_end":
+        t_end = float("inf")
+    elif case == "state_bytes":
+        sb = 8
+    fake = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+    rc = ssa.lib().ssa_tau_run(m.handle, 4, 0, x0.ctypes.data, t_end, tau, 3, st.ctypes.data, prec, rnd, 0, 0, sb,
+                               fake, fake, None, None, None)
+    assert rc == ssa.SSA_EINVAL
+    assert ssa.lib().ssa_last_error()
+
+
+def test_tau_run_empty_ensemble_is_a_no_op(ssa):
+    m = ssa.Model.from_dict(P.birth_death())
+    x0 = np.zeros(1, np.int32)
+    st = np.array([10.0])
+    rc = ssa.lib().ssa_tau_run(m.handle, 0, 0, x0.ctypes.data, 10.0, 0.5, 1, st.ctypes.data, 0, 0, 0, 0, 4,
+                               None, None, None, None, None)
+    assert rc == ssa.SSA_OK

@@ -162,22 +162,31 @@ def test_host_entry_point_matches_device(ssa):
     assert_same({**h, "status": h["status"].view(np.int32)}, {**g, "status": g["status"].view(np.uint32)})
 
 
-def test_full_size_schlogl_sampled_trajectories(ssa):
+BENCH_MODES = [("mixed_f16", "rn"), ("mixed_bf16", "rn"), ("uniform_f16", "rn"), ("uniform_f16", "sr"),
+               ("uniform_bf16", "sr"), ("uniform_f16", "sra"), ("mixed_f16", "sr")]
+
+
+@pytest.mark.parametrize("prec,rnd", BENCH_MODES)
+def test_full_size_schlogl_sampled_trajectories(ssa, prec, rnd):
     """The benchmark's workload (10^6 Schloegl trajectories, 50 snapshots,
-    t_end = 10) in its launch configuration; 24 trajectory ids spread over the
-    range are recomputed one by one on the oracle."""
+    t_end = 10, reservoirs folded, 2e5-event cap) in its launch configuration;
+    24 trajectory ids spread over the range are recomputed one by one on the
+    oracle, including the last id."""
     m = P.schlogl()
     x0 = P.schlogl_x0(m)
     n = 1_000_000
     samples = P.even_samples(10.0, 50)
-    g, _ = gpu_run(ssa, m, x0, n, 10.0, samples, "mixed_f16", "sr", True, 11, 10**7)
-    assert np.all(g["status"] == 0)
+    g, _ = gpu_run(ssa, m, x0, n, 10.0, samples, prec, rnd, True, 2605, 200000)
     ids = np.linspace(0, n - 1, 24).astype(np.int64)
     for r in ids:
-        o = oracle.run(m, x0, 1, 10.0, samples, "mixed_f16", "sr", True, 11, 10**7, g0=int(r))
+        o = oracle.run(m, x0, 1, 10.0, samples, prec, rnd, True, 2605, 200000, g0=int(r))
         np.testing.assert_array_equal(g["snapshots"][:, :, r], o["snapshots"][:, :, 0])
         assert g["n_events"][r] == o["n_events"][0]
+        assert g["status"][r] == o["status"][0]
         assert g["t_final"][r] == o["t_final"][0]
-    # property over the whole ensemble: mass at both Schloegl modes
-    xs = g["snapshots"][-1, 0]
-    assert np.mean(xs < 250) > 0.2 and np.mean(xs > 400) > 0.2
+    # properties over the whole ensemble: conservation of the reservoirs, valid statuses
+    assert np.all(g["snapshots"][:, 1:, :] == x0[1:][None, :, None])
+    assert np.all((g["status"] & ~2) == 0)
+    if rnd != "rn" or prec.startswith("mixed"):
+        xs = g["snapshots"][-1, 0]
+        assert np.mean(xs < 250) > 0.2 and np.mean(xs > 400) > 0.1

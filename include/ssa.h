@@ -164,7 +164,7 @@ int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_
 
 /*
  * ssa_tau_run -- explicit tau-leaping with a fixed leap (the approximate
- * methods of Sec. 1 and Sec. 2, run in the reduced-precision modes; Sec. 5
+ * family of Table 1 and Sec. 2, run in the reduced-precision modes; Sec. 5
  * lists this interaction as untested and Sec. 6 as future work).  Leap n covers
  * [n tau, (n+1) tau), n = 0 .. ceil(t_end / tau) - 1; in each leap every
  * reaction j fires k_j ~ Poisson(a_j(x) tau) times at once and

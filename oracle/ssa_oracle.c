@@ -796,7 +796,7 @@ void oracle_philox_array(const uint32_t ctr[4], const uint32_t key[2], int64_t n
 /* ======================================================================== */
 /* Mixed-precision tau-leaping (the paper names the combination of reduced  */
 /* precision with tau-leaping as future work, Sec. 5 and Sec. 6; explicit    */
-/* tau-leaping is the approximate method of its Table "taxonomy").           */
+/* tau-leaping is the approximate family of its Table 1).                   */
 /*                                                                           */
 /* Readings:                                                                 */
 /*  T1 fixed leap size tau; leap n covers [n tau, (n+1) tau); L =            */

@@ -1,8 +1,8 @@
 // tau_device.cuh -- mixed-precision tau-leaping on the GPU.
 //
-// Explicit tau-leaping (the approximate method of the paper's Table
-// "taxonomy"; its combination with reduced precision is the paper's stated
-// future work): with a fixed leap tau, each leap fires k_j ~ Poisson(a_j tau)
+// Explicit tau-leaping (the approximate family of the paper's Table 1; its
+// combination with reduced precision is untested there, Sec. 5, and named as
+// future work, Sec. 6): with a fixed leap tau, each leap fires k_j ~ Poisson(a_j tau)
 // of every channel at once, x += sum_j nu_j k_j.  Contract (shared with the
 // oracle, written independently):
 //  * leap n covers [n tau, (n+1) tau), L = ceil(t_end / tau) leaps; the leap

@@ -83,13 +83,13 @@ def ops_per_event(prec, rnd):
 
 # ------------------------------------------------------------ ncu traffic
 # DRAM bytes (read + write) per trajectory of the step's kernels, from one ncu
-# capture (profiles/ssa_kernel_schlogl_*.md; a 3e5-trajectory launch scaled
+# capture (the uniform_f16 RN kernel profile; a 3e5-trajectory launch scaled
 # per trajectory: the traffic is the snapshot stream, proportional to the
 # trajectories).  Valid only for the kernel source it was measured on: the
 # key includes a hash of the device code, and a changed kernel reports null.
 NCU_TRAFFIC_PER_TRAJ = {
-    # uniform_f16 RN, 3e5 trajectories: 279,794,432 B read + 443,069,184 B written
-    ("d6789f7569202092", "uniform_f16:rn"): (279794432 + 443069184) / 300000,
+    # uniform_f16 RN, 3e5 trajectories: 272,201,216 B read + 446,491,136 B written
+    ("95b12a1602e75ec8", "uniform_f16:rn"): (272201216 + 446491136) / 300000,
 }
 
 

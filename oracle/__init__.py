@@ -241,3 +241,50 @@ def tau_run(model, x0, n_traj, t_end, tau, sample_times, precision="fp64", round
     if rc != 0:
         raise ValueError("oracle_tau_run rejected its arguments")
     return {"snapshots": out, "status": status, "n_events": nev, "t_final": tf}
+
+
+def _rdme_lib():
+    L = lib()
+    if not getattr(L, "_rdme_ready", False):
+        P = ctypes.c_void_p
+        i, i64, u64, d = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        L.oracle_rdme_run.restype = i
+        L.oracle_rdme_run.argtypes = [i, i, P, P, P, P, P, P, i, i, i, P, P, i64, u64, d, i, P, i, i, i, u64, i64, i,
+                                      P, P, P, P]
+        L._rdme_ready = True
+    return L
+
+
+def rdme_run(model, dims, diffusion, x0, n_traj, t_end, sample_times, precision="fp64", rounding="rn",
+             normalise=False, seed=0, max_events=10**9, state_bytes=4, g0=0):
+    """RDME trajectories on an nx x ny x nz lattice (dims) with hop rates per
+    direction ``diffusion`` [N] and initial counts ``x0`` [S, N]; snapshots
+    [K, S, N, n_traj] plus status, n_events (reactions and hops), t_final."""
+    order = np.ascontiguousarray(model["order"], dtype=np.int32)
+    M, N = order.shape
+    stoich = np.ascontiguousarray(model["stoich"], dtype=np.int32)
+    rate = np.ascontiguousarray(model["rate"], dtype=np.float64)
+    law = np.ascontiguousarray(model.get("law", np.zeros(M)), dtype=np.int32)
+    hill = model.get("hill")
+    hill = None if hill is None else np.ascontiguousarray(hill, dtype=np.float64).reshape(M, 4)
+    const = model.get("constant")
+    const = None if const is None else np.ascontiguousarray(const, dtype=np.uint8)
+    nx, ny, nz = (list(dims) + [1, 1])[:3]
+    S = nx * ny * nz
+    x0 = np.ascontiguousarray(np.broadcast_to(np.asarray(x0, dtype=np.int32), (S, N)))
+    D = np.ascontiguousarray(diffusion, dtype=np.float64)
+    st = np.ascontiguousarray(sample_times, dtype=np.float64)
+    K = st.size
+    out = np.zeros((K, S, N, n_traj), dtype=np.int16 if state_bytes == 2 else np.int32)
+    status = np.zeros(n_traj, dtype=np.uint32)
+    nev = np.zeros(n_traj, dtype=np.int64)
+    tf = np.zeros(n_traj, dtype=np.float64)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    rnd = ROUNDINGS[rounding] if isinstance(rounding, str) else int(rounding)
+    rc = _rdme_lib().oracle_rdme_run(N, M, _p(order), _p(stoich), _p(rate), _p(law), _p(hill), _p(const), nx, ny, nz,
+                                     _p(D), _p(x0), int(n_traj), int(g0), float(t_end), K, _p(st), prec, rnd,
+                                     int(bool(normalise)), int(seed) & 0xFFFFFFFFFFFFFFFF, int(max_events),
+                                     int(state_bytes), _p(out), _p(status), _p(nev), _p(tf))
+    if rc != 0:
+        raise ValueError("oracle_rdme_run rejected its arguments")
+    return {"snapshots": out, "status": status, "n_events": nev, "t_final": tf}

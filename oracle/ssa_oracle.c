@@ -1170,3 +1170,467 @@ void oracle_exp_f64_array(const double *x, int64_t n, double *out)
 {
     for (int64_t i = 0; i < n; ++i) out[i] = oracle_exp_f64(x[i]);
 }
+
+/* ======================================================================== */
+/* Reaction-diffusion master equation (RDME) on a Cartesian lattice.  The    */
+/* paper names the RDME -- well-mixed voxels whose reactions follow the SSA, */
+/* coupled by stochastic hops between neighbours -- as the spatial setting   */
+/* its question extends to (Sec. 1, Sec. 5, future work in Sec. 6); it gives */
+/* no algorithm.  Readings (the CUDA engine implements the same contract):   */
+/*  D1 lattice nx x ny x nz, voxel v = ix + nx (iy + ny iz); reflecting       */
+/*     boundaries; hop directions in the order -x, +x, -y, +y, -z, +z.        */
+/*  D2 channels of voxel v, in order: reactions j = 0..M-1 (the well-mixed   */
+/*     propensity chain on x_v, reading R3), then for each species i with     */
+/*     D_i > 0 (ascending) and each existing neighbour direction: the hop    */
+/*     (i, dir), an order-1 channel of rate D_i: h = rnd(D_i' * rnd(x_vi)),   */
+/*     zero when x_vi < 1; the two operations are computed once per species  */
+/*     and the value repeats for each direction.  D_i' is D_i rounded once    */
+/*     to the propensity type (RN), like c'_j.                                */
+/*  D3 voxel total L_v = last partial sum S_C of its channels (S_1 = first   */
+/*     channel value, S_c = S_{c-1} + value_c in the accumulator type).       */
+/*  D4 sum tree: T = smallest power of two >= S leaves (padding leaves = 0), */
+/*     heap order (node 1 the root, children 2q and 2q+1, leaf v at T + v);  */
+/*     node q = left + right in the accumulator type; a0 = node 1.            */
+/*  D5 event n: u1, u2, E, tau, target and t_new exactly as the well-mixed   */
+/*     step (R6, R7); voxel by descent from the root with r = target: if      */
+/*     left > r go left; else if right > 0 then r = r - left (accumulator     */
+/*     type) and go right; else go left.  Channel within the voxel: smallest  */
+/*     c with S_c > r, else the last channel with a positive value.          */
+/*  D6 after an event the changed voxel(s) (one for a reaction, source and   */
+/*     destination for a hop) are recomputed, then their ancestors, bottom-  */
+/*     up, each node once.  Values are cached between events: a voxel's      */
+/*     partial sums are recomputed for the selection from its state and the  */
+/*     epoch at which it was last computed, which reproduces them exactly.   */
+/*  D7 stochastic rounding bits (16-bit SR modes), 16 bits per operation as  */
+/*     R5, from Philox counters (block lo, block hi, trajectory id, tag):     */
+/*     voxel v computed at epoch e (0 = initial state, n + 1 = after event   */
+/*     n): tag 0x80000000 | v, block = e * 2^32 + op / 8, operations in      */
+/*     channel order (reaction chains, hop pairs, then the partial sums in   */
+/*     uniform modes); tree node q at epoch e (uniform modes): tag            */
+/*     0x40000000 | q, block e * 2^32, operation 0; event-level operations   */
+/*     of event n (uniform modes): stream 1, B = ceil((5 + log2 T) / 8)      */
+/*     blocks per event, slots E, U2, tau, target, t_new, then one slot per   */
+/*     descent level.  Mixed modes round only the channel chains.             */
+/*  D8 snapshots out[k][v][i][trajectory]; stops and status as R9; the       */
+/*     event count includes hops.  With S = 1 the method is the well-mixed   */
+/*     direct method operation for operation (RN modes and fp32/fp64).        */
+/* ======================================================================== */
+#define OR_MAX_S 4096
+#define OR_MAX_CH (OR_MAX_M + 6 * OR_MAX_N)
+
+typedef struct {
+    int nx, ny, nz, S, T, depth;
+    double D[OR_MAX_N];
+} olattice;
+
+static int lat_neighbour(const olattice *L, int v, int dir)
+{
+    int ix = v % L->nx, iy = (v / L->nx) % L->ny, iz = v / (L->nx * L->ny);
+    switch (dir) {
+    case 0: return ix > 0 ? v - 1 : -1;
+    case 1: return ix < L->nx - 1 ? v + 1 : -1;
+    case 2: return iy > 0 ? v - L->nx : -1;
+    case 3: return iy < L->ny - 1 ? v + L->nx : -1;
+    case 4: return iz > 0 ? v - L->nx * L->ny : -1;
+    default: return iz < L->nz - 1 ? v + L->nx * L->ny : -1;
+    }
+}
+
+typedef struct {
+    void *out;
+    int state_bytes;
+    int64_t n_traj, col;
+    int S, N;
+} lsink;
+
+static void write_lattice(const lsink *s, int k, const int32_t *x, uint32_t *status)
+{
+    for (int v = 0; v < s->S; ++v)
+        for (int i = 0; i < s->N; ++i) {
+            int64_t idx = (((int64_t)k * s->S + v) * s->N + i) * s->n_traj + s->col;
+            int32_t val = x[v * s->N + i];
+            if (s->state_bytes == 2) {
+                if (val > 32767) { val = 32767; *status |= ST_STATE_RANGE; }
+                if (val < -32768) { val = -32768; *status |= ST_STATE_RANGE; }
+                ((int16_t *)s->out)[idx] = (int16_t)val;
+            } else {
+                ((int32_t *)s->out)[idx] = val;
+            }
+        }
+}
+
+/* Hop channel c >= M of voxel v: the species and the destination voxel. */
+static void hop_channel(const omodel *md, const olattice *L, int v, int c, int *species, int *dest)
+{
+    int idx = c - md->M;
+    for (int i = 0; i < md->N; ++i) {
+        if (!(L->D[i] > 0.0)) continue;
+        for (int dir = 0; dir < 6; ++dir) {
+            int w = lat_neighbour(L, v, dir);
+            if (w < 0) continue;
+            if (idx == 0) { *species = i; *dest = w; return; }
+            idx -= 1;
+        }
+    }
+    *species = -1; *dest = -1;
+}
+
+static int n_neighbours(const olattice *L, int v)
+{
+    int c = 0;
+    for (int dir = 0; dir < 6; ++dir) c += lat_neighbour(L, v, dir) >= 0;
+    return c;
+}
+
+/* Voxel v in binary64 (D2, D3).  Returns L_v; when sel is not NULL, also   */
+/* the selected channel for residual target r (D5).                        */
+static double voxel_f64(const omodel *md, const olattice *L, const int32_t *xv, int v, const double *cp,
+                        const double *h0, const double *h1, double r, int *sel)
+{
+    double val[OR_MAX_CH], Ssum[OR_MAX_CH];
+    int C = 0;
+    for (int j = 0; j < md->M; ++j) val[C++] = prop_f64(md, j, xv, cp, h0, h1);
+    int nnb = n_neighbours(L, v);
+    if (nnb > 0)
+        for (int i = 0; i < md->N; ++i) {
+            if (!(L->D[i] > 0.0)) continue;
+            double h = xv[i] < 1 ? 0.0 : L->D[i] * (double)xv[i];
+            for (int d = 0; d < nnb; ++d) val[C++] = h;
+        }
+    Ssum[0] = val[0];
+    for (int c = 1; c < C; ++c) Ssum[c] = Ssum[c - 1] + val[c];
+    if (sel) {
+        int mu = -1;
+        for (int c = 0; c < C; ++c) if (Ssum[c] > r) { mu = c; break; }
+        if (mu < 0) for (int c = C - 1; c >= 0; --c) if (val[c] > 0.0) { mu = c; break; }
+        *sel = mu;
+    }
+    return Ssum[C - 1];
+}
+
+/* Voxel v in binary32 arithmetic: kind 0 fp32, 1 mixed (16-bit channel      */
+/* values), 2 uniform (16-bit values and sums).  R points at the voxel's SR  */
+/* stream for this epoch (op = 0).                                            */
+static float voxel_f32(const omodel *md, const olattice *L, const int32_t *xv, int v, const float *cp,
+                       const float *h0, const float *h1, const float *Dp, int kind, rounder *R, float r, int *sel)
+{
+    float val[OR_MAX_CH], Ssum[OR_MAX_CH];
+    int C = 0;
+    for (int j = 0; j < md->M; ++j)
+        val[C++] = kind == 0 ? prop_f32(md, j, xv, cp, h0, h1) : prop_16(md, j, xv, cp, h0, h1, R);
+    int nnb = n_neighbours(L, v);
+    if (nnb > 0)
+        for (int i = 0; i < md->N; ++i) {
+            if (!(L->D[i] > 0.0)) continue;
+            float h;
+            if (kind == 0) {
+                h = xv[i] < 1 ? 0.0f : Dp[i] * (float)xv[i];
+            } else if (xv[i] < 1) {
+                h = 0.0f;
+                R->op += 2;                 /* slots reserved, as for a short reactant */
+            } else {
+                float f = rnd16(R, (float)xv[i]);
+                h = rnd16(R, Dp[i] * f);
+            }
+            for (int d = 0; d < nnb; ++d) val[C++] = h;
+        }
+    Ssum[0] = val[0];
+    for (int c = 1; c < C; ++c) Ssum[c] = kind == 2 ? rnd16(R, Ssum[c - 1] + val[c]) : Ssum[c - 1] + val[c];
+    if (sel) {
+        int mu = -1;
+        for (int c = 0; c < C; ++c) if (Ssum[c] > r) { mu = c; break; }
+        if (mu < 0) for (int c = C - 1; c >= 0; --c) if (val[c] > 0.0f) { mu = c; break; }
+        *sel = mu;
+    }
+    return Ssum[C - 1];
+}
+
+static void set_tag(word_stream *ws, uint32_t tag)
+{
+    ws->stream = tag;
+    ws->have = 0;
+}
+
+/* Apply channel c of voxel v; returns the second changed voxel (hop) or -1. */
+static int rdme_apply(const omodel *md, const olattice *L, int v, int c, int32_t *x, uint32_t *status)
+{
+    const int N = md->N;
+    if (c < md->M) {
+        apply_event(md, c, x + v * N, status);
+        return -1;
+    }
+    int i, w;
+    hop_channel(md, L, v, c, &i, &w);
+    x[v * N + i] -= 1;
+    x[w * N + i] += 1;
+    if (x[v * N + i] < 0) *status |= ST_STATE_RANGE;
+    return w;
+}
+
+/* One RDME trajectory in binary64. */
+static void rdme_traj_f64(const omodel *md, const olattice *L, const runp *rp, word_stream *ws, int32_t *x,
+                          double *node, const lsink *snk, uint32_t *status, int64_t *n_events, double *t_final)
+{
+    const int N = md->N, S = L->S, T = L->T;
+    double cp[OR_MAX_M], h0[OR_MAX_M], h1[OR_MAX_M];
+    for (int j = 0; j < md->M; ++j) {
+        cp[j] = md->cprime[j];
+        h0[j] = md->law[j] == LAW_HILL ? md->hill[4 * j] : 0.0;
+        h1[j] = md->law[j] == LAW_HILL ? md->hill[4 * j + 1] : 0.0;
+    }
+    for (int v = 0; v < T; ++v) node[T + v] = v < S ? voxel_f64(md, L, x + v * N, v, cp, h0, h1, 0.0, NULL) : 0.0;
+    for (int q = T - 1; q >= 1; --q) node[q] = node[2 * q] + node[2 * q + 1];
+    double t = 0.0;
+    int64_t n = 0;
+    int k = 0;
+    for (;;) {
+        if (n >= rp->max_events) { *status |= ST_MAX_EVENTS; break; }
+        double a0 = node[1];
+        if (f64_is_nan(a0)) { *status |= ST_NAN; break; }
+        if (f64_is_inf(a0)) { *status |= ST_OVERFLOW; break; }
+        if (a0 == 0.0) break;
+        uint64_t w = (uint64_t)n * 2u;
+        uint32_t w0 = stream_word(ws, w), w1 = stream_word(ws, w + 1);
+        double u1 = ((double)w0 + 1.0) * 0x1p-32;
+        double u2 = (double)w1 * 0x1p-32;
+        double E = -oracle_log_f64(u1);
+        double tau = E / a0;
+        double target = u2 * a0;
+        double t_new = t + tau;
+        while (k < rp->K && rp->samples[k] < t_new) write_lattice(snk, k++, x, status);
+        if (t_new > rp->t_end) break;
+        int q = 1;
+        double r = target;
+        while (q < T) {
+            double lf = node[2 * q], rt = node[2 * q + 1];
+            if (lf > r) q = 2 * q;
+            else if (rt > 0.0) { r = r - lf; q = 2 * q + 1; }
+            else q = 2 * q;
+        }
+        int v = q - T, c = -1;
+        voxel_f64(md, L, x + v * N, v, cp, h0, h1, r, &c);
+        int w2 = rdme_apply(md, L, v, c, x, status);
+        t = t_new;
+        n += 1;
+        if (*status & ST_STATE_RANGE) break;
+        node[T + v] = voxel_f64(md, L, x + v * N, v, cp, h0, h1, 0.0, NULL);
+        if (w2 >= 0) node[T + w2] = voxel_f64(md, L, x + w2 * N, w2, cp, h0, h1, 0.0, NULL);
+        /* ancestors, level by level; qb = 0 once the two paths have merged */
+        int qa = (T + v) >> 1, qb = w2 >= 0 ? (T + w2) >> 1 : 0;
+        while (qa >= 1) {
+            if (qb == qa) qb = 0;
+            node[qa] = node[2 * qa] + node[2 * qa + 1];
+            if (qb) node[qb] = node[2 * qb] + node[2 * qb + 1];
+            qa >>= 1;
+            qb >>= 1;
+        }
+    }
+    while (k < rp->K) write_lattice(snk, k++, x, status);
+    *n_events = n;
+    *t_final = t;
+}
+
+/* Node q of the tree at epoch e in binary32 arithmetic (kind as voxel_f32). */
+static float tree_node_f32(const float *node, int q, int kind, int fmt, int sr, word_stream *wsn, uint32_t e)
+{
+    float s = node[2 * q] + node[2 * q + 1];
+    if (kind != 2) return s;
+    rounder R;
+    set_tag(wsn, 0x40000000u | (uint32_t)q);
+    R.bf16 = fmt; R.sr = sr; R.ws = wsn; R.sr_base = (uint64_t)e << 34; R.op = 0;
+    return rnd16(&R, s);
+}
+
+/* Voxel v at epoch e in binary32 arithmetic, with its SR stream. */
+static float voxel_at_f32(const omodel *md, const olattice *L, const int32_t *x, int v, uint32_t e, const float *cp,
+                          const float *h0, const float *h1, const float *Dp, int kind, int fmt, int sr,
+                          word_stream *wsv, float r, int *sel)
+{
+    rounder R;
+    set_tag(wsv, 0x80000000u | (uint32_t)v);
+    R.bf16 = fmt; R.sr = sr; R.ws = wsv; R.sr_base = (uint64_t)e << 34; R.op = 0;
+    return voxel_f32(md, L, x + v * md->N, v, cp, h0, h1, Dp, kind, &R, r, sel);
+}
+
+/* One RDME trajectory in binary32 arithmetic: kind 0 fp32, 1 mixed, 2 uniform. */
+static void rdme_traj_f32(const omodel *md, const olattice *L, const runp *rp, word_stream *ws, word_stream *wsr,
+                          word_stream *wsv, word_stream *wsn, int32_t *x, float *node, uint32_t *epoch,
+                          const lsink *snk, uint32_t *status, int64_t *n_events, double *t_final,
+                          int kind, int fmt, int sr)
+{
+    const int N = md->N, S = L->S, T = L->T;
+    float cp[OR_MAX_M], h0[OR_MAX_M], h1[OR_MAX_M], Dp[OR_MAX_N];
+    for (int j = 0; j < md->M; ++j) {
+        cp[j] = (float)md->cprime[j];
+        h0[j] = md->law[j] == LAW_HILL ? (float)md->hill[4 * j] : 0.0f;
+        h1[j] = md->law[j] == LAW_HILL ? (float)md->hill[4 * j + 1] : 0.0f;
+        if (kind != 0) { cp[j] = rn16(fmt, cp[j]); h0[j] = rn16(fmt, h0[j]); h1[j] = rn16(fmt, h1[j]); }
+    }
+    for (int i = 0; i < N; ++i) Dp[i] = kind != 0 ? rn16(fmt, (float)L->D[i]) : (float)L->D[i];
+    float t_end = kind == 2 ? rn16(fmt, (float)rp->t_end) : (float)rp->t_end;
+    float smp[1024];
+    for (int kk = 0; kk < rp->K; ++kk) smp[kk] = kind == 2 ? rn16(fmt, (float)rp->samples[kk]) : (float)rp->samples[kk];
+    const int nsr_ev = 5 + L->depth;
+    const uint64_t Ws_ev = 4u * (uint64_t)((nsr_ev + 7) / 8);
+    rounder Re;
+    Re.bf16 = fmt; Re.sr = sr; Re.ws = wsr; Re.sr_base = 0; Re.op = 0;
+
+    for (int v = 0; v < T; ++v) {
+        node[T + v] = v < S ? voxel_at_f32(md, L, x, v, 0u, cp, h0, h1, Dp, kind, fmt, sr, wsv, 0.0f, NULL) : 0.0f;
+        if (v < S) epoch[v] = 0;
+    }
+    for (int q = T - 1; q >= 1; --q) node[q] = tree_node_f32(node, q, kind, fmt, sr, wsn, 0u);
+    float t = 0.0f;
+    int64_t n = 0;
+    int k = 0;
+    for (;;) {
+        if (n >= rp->max_events) { *status |= ST_MAX_EVENTS; break; }
+        float a0 = node[1];
+        if (f32_is_nan(a0)) { *status |= ST_NAN; break; }
+        if (f32_is_inf(a0)) { *status |= ST_OVERFLOW; break; }
+        if (a0 == 0.0f) break;
+        uint64_t w = (uint64_t)n * 2u;
+        uint32_t w0 = stream_word(ws, w), w1 = stream_word(ws, w + 1);
+        float u1 = (float)((w0 >> 8) + 1u) * 0x1p-24f;
+        float u2 = (float)(w1 >> 8) * 0x1p-24f;
+        float tau, target, t_new;
+        Re.sr_base = (uint64_t)n * Ws_ev;
+        if (kind == 2) {
+            Re.op = 0;
+            float E = rnd16(&Re, -oracle_log_f32(u1));
+            float U2 = rnd16(&Re, u2);
+            tau = rnd16(&Re, E / a0);
+            target = rnd16(&Re, U2 * a0);
+            t_new = rnd16(&Re, t + tau);
+        } else {
+            float E = -oracle_log_f32(u1);
+            tau = E / a0;
+            target = u2 * a0;
+            t_new = t + tau;
+        }
+        while (k < rp->K && smp[k] < t_new) write_lattice(snk, k++, x, status);
+        if (t_new > t_end) break;
+        int q = 1, level = 0;
+        float r = target;
+        while (q < T) {
+            float lf = node[2 * q], rt = node[2 * q + 1];
+            if (lf > r) {
+                q = 2 * q;
+            } else if (rt > 0.0f) {
+                if (kind == 2) { Re.op = 5 + level; r = rnd16(&Re, r - lf); }
+                else r = r - lf;
+                q = 2 * q + 1;
+            } else {
+                q = 2 * q;
+            }
+            level += 1;
+        }
+        int v = q - T, c = -1;
+        voxel_at_f32(md, L, x, v, epoch[v], cp, h0, h1, Dp, kind, fmt, sr, wsv, r, &c);
+        int w2 = rdme_apply(md, L, v, c, x, status);
+        t = t_new;
+        n += 1;
+        if (*status & ST_STATE_RANGE) break;
+        const uint32_t e = (uint32_t)n;            /* epoch n + 1 of the event just applied */
+        node[T + v] = voxel_at_f32(md, L, x, v, e, cp, h0, h1, Dp, kind, fmt, sr, wsv, 0.0f, NULL);
+        epoch[v] = e;
+        if (w2 >= 0) {
+            node[T + w2] = voxel_at_f32(md, L, x, w2, e, cp, h0, h1, Dp, kind, fmt, sr, wsv, 0.0f, NULL);
+            epoch[w2] = e;
+        }
+        int qa = (T + v) >> 1, qb = w2 >= 0 ? (T + w2) >> 1 : 0;
+        while (qa >= 1) {
+            if (qb == qa) qb = 0;
+            node[qa] = tree_node_f32(node, qa, kind, fmt, sr, wsn, e);
+            if (qb) node[qb] = tree_node_f32(node, qb, kind, fmt, sr, wsn, e);
+            qa >>= 1;
+            qb >>= 1;
+        }
+    }
+    while (k < rp->K) write_lattice(snk, k++, x, status);
+    *n_events = n;
+    *t_final = (double)t;
+}
+
+/* Public entry: RDME trajectories g0 .. g0+n_traj-1 on an nx x ny x nz      */
+/* lattice; D [N] hop rates per direction; x0 [S][N]; snapshots               */
+/* out[((k*S + v)*N + i)*n_traj + r].  Returns 0, or -1 on invalid arguments. */
+int oracle_rdme_run(int N, int M, const int32_t *order, const int32_t *stoich, const double *rate,
+                    const int32_t *law, const double *hill, const uint8_t *constant, int nx, int ny, int nz,
+                    const double *D, const int32_t *x0, int64_t n_traj, uint64_t g0, double t_end, int K,
+                    const double *samples, int precision, int rounding, int normalise, uint64_t seed,
+                    int64_t max_events, int state_bytes, void *out, uint32_t *status, int64_t *n_events,
+                    double *t_final)
+{
+    if (N < 1 || N > OR_MAX_N || M < 1 || M > OR_MAX_M || K < 0 || K > 1024) return -1;
+    if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz > OR_MAX_S) return -1;
+    if (precision < 0 || precision > 5 || rounding < 0 || rounding > 1) return -1;
+    if (rounding == 1 && precision < 2) return -1;
+    if (state_bytes != 2 && state_bytes != 4) return -1;
+    if (n_traj < 0 || g0 + (uint64_t)n_traj > 0x100000000ull) return -1;
+    if (max_events < 0 || max_events > 4294967294ll) return -1;
+    olattice L;
+    memset(&L, 0, sizeof(L));
+    L.nx = nx; L.ny = ny; L.nz = nz; L.S = nx * ny * nz;
+    L.T = 1; L.depth = 0;
+    while (L.T < L.S) { L.T *= 2; L.depth += 1; }
+    for (int i = 0; i < N; ++i) {
+        if (!(D[i] >= 0.0) || f64_is_inf(D[i])) return -1;
+        if (constant && constant[i] && D[i] != 0.0) return -1;
+        L.D[i] = D[i];
+        if (constant && constant[i])
+            for (int v = 1; v < L.S; ++v) if (x0[v * N + i] != x0[i]) return -1;
+    }
+    omodel md;
+    memset(&md, 0, sizeof(md));
+    md.N = N; md.M = M; md.order = order; md.stoich = stoich; md.law = law;
+    md.hill = hill; md.constant = constant; md.normalise = normalise;
+    for (int j = 0; j < M; ++j) {
+        if (law[j] == LAW_HILL) { md.cprime[j] = 0.0; continue; }
+        double denom = 1.0;
+        for (int i = 0; i < N; ++i) denom = denom * factorial(order[j * N + i]);
+        double c = rate[j] / denom;
+        if (normalise && constant) {
+            for (int i = 0; i < N; ++i) {
+                if (!constant[i] || order[j * N + i] == 0) continue;
+                for (int m = 0; m < order[j * N + i]; ++m) c = c * (double)(x0[i] - m);
+                md.folded[j][i] = 1;
+            }
+        }
+        md.cprime[j] = c;
+    }
+    runp rp;
+    rp.t_end = t_end; rp.K = K; rp.samples = samples; rp.max_events = max_events;
+    int32_t *x = (int32_t *)malloc(sizeof(int32_t) * (size_t)L.S * (size_t)N);
+    double *node64 = (double *)malloc(sizeof(double) * 2 * (size_t)L.T);
+    float *node32 = (float *)malloc(sizeof(float) * 2 * (size_t)L.T);
+    uint32_t *epoch = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)L.S);
+    if (!x || !node64 || !node32 || !epoch) { free(x); free(node64); free(node32); free(epoch); return -1; }
+    for (int64_t r = 0; r < n_traj; ++r) {
+        word_stream ws, wsr, wsv, wsn;
+        memset(&ws, 0, sizeof(ws));
+        ws.key[0] = (uint32_t)seed;
+        ws.key[1] = (uint32_t)(seed >> 32);
+        ws.traj = (uint32_t)(g0 + (uint64_t)r);
+        ws.stream = 0;
+        wsr = ws; wsr.stream = 1;
+        wsv = ws; wsn = ws;
+        memcpy(x, x0, sizeof(int32_t) * (size_t)L.S * (size_t)N);
+        lsink snk;
+        snk.out = out; snk.state_bytes = state_bytes; snk.n_traj = n_traj; snk.col = r; snk.S = L.S; snk.N = N;
+        uint32_t st = 0;
+        int64_t ne = 0;
+        double tf = 0.0;
+        const int fmt = (precision == P_MIXED_BF16 || precision == P_UNIFORM_BF16) ? 1 : 0;
+        if (precision == P_FP64)
+            rdme_traj_f64(&md, &L, &rp, &ws, x, node64, &snk, &st, &ne, &tf);
+        else
+            rdme_traj_f32(&md, &L, &rp, &ws, &wsr, &wsv, &wsn, x, node32, epoch, &snk, &st, &ne, &tf,
+                          precision == P_FP32 ? 0 : (precision >= P_UNIFORM_F16 ? 2 : 1), fmt, rounding);
+        if (status) status[r] = st;
+        if (n_events) n_events[r] = ne;
+        if (t_final) t_final[r] = tf;
+    }
+    free(x); free(node64); free(node32); free(epoch);
+    return 0;
+}

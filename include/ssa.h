@@ -200,6 +200,47 @@ int ssa_tau_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, co
                 uint32_t *traj_status, int64_t *n_events, double *t_final, void *stream);
 
 /*
+ * ssa_rdme_run -- reaction-diffusion master equation on an nx x ny x nz
+ * lattice of well-mixed voxels (the spatial setting of Sec. 1 and Sec. 5,
+ * future work in Sec. 6; the paper gives no algorithm).  Every voxel runs the
+ * model's reactions; species i hops to each existing neighbour (reflecting
+ * boundaries) at rate diffusion[i] * x_vi.  One trajectory = one lattice,
+ * simulated exactly by the direct method over all channels of all voxels:
+ *   channels of voxel v  reactions 0..M-1 (the propensity chain of
+ *                        ssa_ensemble_run on the voxel's counts), then for
+ *                        each species with diffusion > 0 and each existing
+ *                        neighbour direction (-x, +x, -y, +y, -z, +z) a hop
+ *                        of value rnd(D_i * rnd(x_vi))
+ *   selection            voxel totals (last partial sum, accumulator type) in
+ *                        a binary sum tree; descent from the root with
+ *                        r = u2 a0 (go right with r = r - left when left <= r
+ *                        and right > 0), then the first channel of the voxel
+ *                        whose partial sum exceeds r
+ *   rounding             as ssa_ensemble_run; stochastic-rounding bits are
+ *                        keyed by (voxel or tree node, epoch of its last
+ *                        recomputation); SSA_SR_ACCUM is rejected
+ * With one voxel the result equals ssa_ensemble_run's in the RN modes.
+ *   nx, ny, nz    lattice extent, each >= 1; S = nx*ny*nz voxels (<= 1024,
+ *                 and the per-lane state -- S*N counts, 2*T tree nodes with T
+ *                 the smallest power of two >= S, S epochs in SR modes --
+ *                 must fit in shared memory for 32 lanes)
+ *   diffusion     host [N] hop rate per direction, finite, >= 0; constant
+ *                 species must have 0 and the same count in every voxel
+ *   x0            host [S][N] initial counts (>= 0), voxel-major
+ *   max_events    events (reactions + hops) per trajectory, 0..2^32-2
+ *   out           device [K][S][N][n_traj], trajectory index fastest
+ *   other arguments as ssa_ensemble_run (n_events counts reactions and hops)
+ * Allocates a work-queue counter and the [S][N] initial-state table with
+ * stream-ordered allocation and frees them after the launch.
+ * Errors: SSA_EINVAL (arguments; lattice too large), SSA_ENOMEM, SSA_ECUDA.
+ */
+int ssa_rdme_run(const ssa_model *model, int nx, int ny, int nz, const double *diffusion, int64_t n_traj,
+                 uint64_t traj_offset, const int32_t *x0, double t_end, int n_samples,
+                 const double *sample_times, int precision, int rounding, int normalise, uint64_t seed,
+                 int64_t max_events, int state_bytes, void *out, uint32_t *traj_status, int64_t *n_events,
+                 double *t_final, void *stream);
+
+/*
  * ssa_set_launch_config -- launch shape for subsequent runs in this process.
  *   threads_per_block  multiple of 32 in 32..256
  *   blocks_per_sm      resident blocks per SM to launch (0 = as many as the

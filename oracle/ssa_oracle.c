@@ -1409,6 +1409,7 @@ static void rdme_traj_f64(const omodel *md, const olattice *L, const runp *rp, w
         }
         int v = q - T, c = -1;
         voxel_f64(md, L, x + v * N, v, cp, h0, h1, r, &c);
+        if (c < 0) { *status |= ST_NAN; break; }   /* unreachable: the descent only enters positive totals */
         int w2 = rdme_apply(md, L, v, c, x, status);
         t = t_new;
         n += 1;
@@ -1527,6 +1528,7 @@ static void rdme_traj_f32(const omodel *md, const olattice *L, const runp *rp, w
         }
         int v = q - T, c = -1;
         voxel_at_f32(md, L, x, v, epoch[v], cp, h0, h1, Dp, kind, fmt, sr, wsv, r, &c);
+        if (c < 0) { *status |= ST_NAN; break; }   /* unreachable: the descent only enters positive totals */
         int w2 = rdme_apply(md, L, v, c, x, status);
         t = t_new;
         n += 1;

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/ssa.h"
+#include "rdme_device.cuh"
 #include "ssa_launch.h"
 #include "ssa_models.h"
 
@@ -364,6 +365,107 @@ int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_
     return rc;
 }
 
+
+int ssa_rdme_run(const ssa_model *model, int nx, int ny, int nz, const double *diffusion, int64_t n_traj,
+                 uint64_t traj_offset, const int32_t *x0, double t_end, int n_samples, const double *sample_times,
+                 int precision, int rounding, int normalise, uint64_t seed, int64_t max_events, int state_bytes,
+                 void *out, uint32_t *traj_status, int64_t *n_events, double *t_final, void *stream)
+{
+    if (!model) return fail(SSA_EINVAL, "model is NULL");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(SSA_EINVAL, "lattice extents must be >= 1");
+    const long long S = (long long)nx * ny * nz;
+    if (S > ssa::kMaxVoxels) return fail(SSA_EINVAL, "lattice has %lld voxels (limit %d)", S, ssa::kMaxVoxels);
+    if (!x0) return fail(SSA_EINVAL, "x0 is NULL");
+    if (!diffusion) return fail(SSA_EINVAL, "diffusion is NULL");
+    const int N = model->N;
+    for (long long v = 0; v < S; ++v)
+        for (int i = 0; i < N; ++i)
+            if (x0[v * N + i] < 0) return fail(SSA_EINVAL, "x0[%lld][%d] is negative", v, i);
+    int rc = validate_run(model, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
+                          max_events, state_bytes);
+    if (rc != SSA_OK) return rc;
+    if (rounding == SSA_SR_ACCUM) return fail(SSA_EINVAL, "the RDME supports SSA_RN and SSA_SR only");
+    if (max_events > 4294967294ll) return fail(SSA_EINVAL, "max_events must be <= 2^32 - 2 for the RDME");
+    for (int i = 0; i < N; ++i) {
+        if (!finite_double(diffusion[i]) || diffusion[i] < 0.0)
+            return fail(SSA_EINVAL, "diffusion[%d] must be finite and >= 0", i);
+        if (model->constant[i]) {
+            if (diffusion[i] != 0.0) return fail(SSA_EINVAL, "constant species %d cannot diffuse", i);
+            for (long long v = 1; v < S; ++v)
+                if (x0[v * N + i] != x0[i])
+                    return fail(SSA_EINVAL, "constant species %d must have the same count in every voxel", i);
+        }
+    }
+    if (n_traj > 0 && (!out || !traj_status)) return fail(SSA_EINVAL, "out and traj_status are required");
+
+    ssa::RdmeArgs *A = new (std::nothrow) ssa::RdmeArgs;
+    if (!A) return fail(SSA_ENOMEM, "out of host memory");
+    std::memset(A, 0, sizeof(*A));
+    fill_structure(*model, normalise, x0, A->a);
+    A->nx = nx;
+    A->ny = ny;
+    A->nz = nz;
+    A->S = (int)S;
+    A->T = 1;
+    A->depth = 0;
+    while (A->T < A->S) {
+        A->T *= 2;
+        A->depth += 1;
+    }
+    for (int i = 0; i < N; ++i) A->D[i] = diffusion[i];
+    A->a.K = n_samples;
+    A->a.n_traj = n_traj;
+    A->a.n_work = n_traj;
+    A->a.slice_pairs = 1;
+    A->a.traj_offset = (uint32_t)traj_offset;
+    A->a.n_sets = 1;
+    A->a.traj_per_set = n_traj;
+    A->a.t_end = t_end;
+    for (int k = 0; k < n_samples; ++k) A->a.samples[k] = sample_times[k];
+    A->a.key0 = (uint32_t)seed;
+    A->a.key1 = (uint32_t)(seed >> 32);
+    A->a.max_events = max_events;
+    A->a.out = out;
+    A->a.state_bytes = state_bytes;
+    A->a.status = traj_status;
+    A->a.n_events = n_events;
+    A->a.t_final = t_final;
+    const int elem = precision == SSA_FP64 ? 8 : 4;
+    const bool epochs = precision >= SSA_MIXED_F16 && rounding == SSA_SR;
+    if (ssa::rdme_block_size(*A, elem, epochs, g_cfg.block) < 32) {
+        delete A;
+        return fail(SSA_EINVAL, "lattice state of %lld voxels x %d species does not fit in shared memory", S, N);
+    }
+    if (n_traj == 0) {
+        delete A;
+        return SSA_OK;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t lat_bytes = sizeof(int32_t) * (size_t)S * (size_t)N;
+    char *d = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d), 256 + lat_bytes, s);
+    if (e != cudaSuccess) {
+        delete A;
+        return e == cudaErrorMemoryAllocation ? fail(SSA_ENOMEM, "RDME tables: out of device memory")
+                                              : cuda_fail(e, "cudaMallocAsync");
+    }
+    A->a.queue_head = reinterpret_cast<unsigned long long *>(d);
+    A->x0_lat = reinterpret_cast<const int32_t *>(d + 256);
+    e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 256, x0, lat_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(d, s);
+        delete A;
+        return cuda_fail(e, "RDME table upload");
+    }
+    int grid = 0, block = 0;
+    e = ssa::launch_rdme(*A, precision, rounding, g_cfg, s, &grid, &block);
+    cudaError_t e2 = cudaFreeAsync(d, s);
+    delete A;
+    if (e != cudaSuccess) return cuda_fail(e, "RDME kernel launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return SSA_OK;
+}
 
 int ssa_tau_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, const int32_t *x0, double t_end,
                 double tau, int n_samples, const double *sample_times, int precision, int rounding, int normalise,

@@ -6,6 +6,7 @@
     python -m paper_2605_00479_gb300.experiments sweeps
     python -m paper_2605_00479_gb300.experiments dwell
     python -m paper_2605_00479_gb300.experiments tau    [n_traj=200000]
+    python -m paper_2605_00479_gb300.experiments rdme   [n_traj=16384] [fp64_traj=2048]
 
 batch: telegraph (kon, koff log-uniform in [0.05, 5], km in [5, 100], gamma 1),
   dimerisation (k1, k2 log-uniform in [x0.5, x2] around 1e-3, 0.1; M0 = 300)
@@ -41,6 +42,12 @@ tau: fixed-leap tau-leaping in reduced precision (the combination the paper
   ensemble (KS p, W1, mean, variance, clamped fraction), and its throughput
   (trajectories/s, leaps/s, reactions/s) next to the direct method's in mixed
   fp16.
+rdme: spatial Schloegl chain -- 32 voxels in a line, each the bistable Schloegl
+  system (reservoirs folded, X0 = 250), X hopping to each neighbour at rate
+  D = 1 per molecule, reflecting ends, t_end = 10, one snapshot at t_end.
+  Every mode's pooled voxel counts against the fp64 ensemble (KS p, W1, mean,
+  variance), the neighbour covariance of X, overflow fraction and events/s
+  (reactions + hops); at most 8e6 events per trajectory.
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -300,11 +307,55 @@ def tau(n_traj=200000, seed=41):
     return out
 
 
+def rdme(n_traj=16384, fp64_traj=2048, seed=51):
+    import torch
+    md = P.schlogl()
+    S = 32
+    x0 = np.tile(P.schlogl_x0(md), (S, 1)).astype(np.int32)
+    D = [1.0, 0.0, 0.0]
+    t_end = 10.0
+    cap = 8 * 10**6          # events per trajectory (about 1.6e6 expected); bounds stagnating clocks
+    m = ssa.Model.from_dict(md)
+    out = {"lattice": [S, 1, 1], "max_events": cap, "diffusion": D, "t_end": t_end, "n_traj": n_traj, "fp64_traj": fp64_traj,
+           "note": "X pooled over voxels at t_end vs the fp64 ensemble (different seed)", "modes": {}}
+    res = {}
+
+    def run(prec, rnd, n, sd):
+        res["r"] = ssa.rdme_run(m, (S,), D, x0, n, t_end, [t_end], prec, rnd, True, sd, cap)
+
+    def summary(r):
+        x = r["snapshots"][0, :, 0, :].cpu().numpy().astype(np.float64)     # [S, n]
+        st = r["status"].cpu().numpy()
+        cov = float(np.mean([np.cov(x[v], x[v + 1])[0, 1] for v in range(S - 1)]))
+        return x, st, cov
+
+    run("fp64", "rn", fp64_traj, seed)
+    dt = _timed(lambda: run("fp64", "rn", fp64_traj, seed))
+    ref, st, cov = summary(res["r"])
+    ev = float(res["r"]["n_events"].double().sum())
+    out["modes"]["fp64:rn"] = {"events_per_s": ev / dt, "time_s": dt, "mean": float(ref.mean()),
+                               "var": float(ref.var()), "neighbour_cov": cov,
+                               "events_per_traj": ev / fp64_traj}
+    ref_pool = ref.ravel()
+    for prec, rnd in [("fp32", "rn"), ("mixed_f16", "rn"), ("mixed_f16", "sr"), ("mixed_bf16", "rn"),
+                      ("uniform_f16", "sr"), ("uniform_bf16", "sr")]:
+        run(prec, rnd, n_traj, seed + 1)
+        dt = _timed(lambda: run(prec, rnd, n_traj, seed + 1))
+        x, st, cov = summary(res["r"])
+        ev = float(res["r"]["n_events"].double().sum())
+        d = _compare(ref_pool, x.ravel())
+        d.update(events_per_s=ev / dt, time_s=dt, neighbour_cov=cov, events_per_traj=ev / n_traj,
+                 overflow=float(np.mean((st & 1) != 0)), capped=float(np.mean((st & 2) != 0)))
+        out["modes"][f"{prec}:{rnd}"] = d
+    torch.cuda.synchronize()
+    return out
+
+
 if __name__ == "__main__":
     cmd = sys.argv[1]
     kw = {}
     for arg in sys.argv[2:]:
         k, v = arg.split("=")
         kw[k] = float(v) if k in ("t_end", "scale") else int(v)
-    fn = {"batch": batch, "scale": scale, "tables": tables, "sweeps": sweeps, "dwell": dwell, "tau": tau}[cmd]
+    fn = {"batch": batch, "scale": scale, "tables": tables, "sweeps": sweeps, "dwell": dwell, "tau": tau, "rdme": rdme}[cmd]
     print(json.dumps(fn(**kw)), flush=True)

@@ -32,6 +32,8 @@ SIGNATURES = {
     "ssa_ensemble_run": (_I, _RUN_ARGS),
     "ssa_ensemble_run_host": (_I, _RUN_ARGS),
     "ssa_tau_run": (_I, [_P, _I64, _U64, _P, _D, _D, _I, _P, _I, _I, _I, _U64, _I, _P, _P, _P, _P, _P]),
+    "ssa_rdme_run": (_I, [_P, _I, _I, _I, _P, _I64, _U64, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, _P, _P, _P, _P,
+                          _P]),
     "ssa_set_launch_config": (_I, [_I, _I, _I]),
     "ssa_batch_create": (_I, [_I, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, ctypes.POINTER(_P)]),
     "ssa_batch_launch": (_I, [_P, _P]),
@@ -226,6 +228,39 @@ def tau_run(model, n_traj, x0, t_end, tau, sample_times, precision="fp64", round
                              _np_ptr(st), prec, rnd, int(bool(normalise)), int(seed) & (2**64 - 1),
                              int(state_bytes), _dev_ptr(out), _dev_ptr(status), _dev_ptr(n_events),
                              _dev_ptr(t_final), ctypes.c_void_p(s.cuda_stream)))
+    return {"snapshots": out, "status": status, "n_events": n_events, "t_final": t_final}
+
+
+def rdme_run(model, dims, diffusion, x0, n_traj, t_end, sample_times, precision="fp64", rounding="rn",
+             normalise=False, seed=0, max_events=10**9, state_bytes=4, out=None, status=None, n_events=None,
+             t_final=None, stream=None, traj_offset=0):
+    """Launch ssa_rdme_run on CUDA tensors: an nx x ny x nz lattice (dims),
+    hop rates ``diffusion`` [N], initial counts ``x0`` [S, N].  Returns
+    snapshots [K, S, N, n_traj], status, n_events (reactions and hops), t_final."""
+    import torch
+    nx, ny, nz = (list(dims) + [1, 1])[:3]
+    S = nx * ny * nz
+    x0 = np.ascontiguousarray(np.broadcast_to(np.asarray(x0, dtype=np.int32), (S, model.N)))
+    D = np.ascontiguousarray(diffusion, dtype=np.float64)
+    if D.shape != (model.N,):
+        raise ValueError("diffusion must have one rate per species")
+    _, st, prec, rnd = _run_scalars(model, n_traj, traj_offset, x0[0], t_end, sample_times, precision, rounding,
+                                    normalise, seed, max_events, state_bytes)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    K = st.size
+    if out is None:
+        out = torch.empty((K, S, model.N, n_traj), dtype=torch.int16 if state_bytes == 2 else torch.int32, device=dev)
+    if status is None:
+        status = torch.empty(n_traj, dtype=torch.int32, device=dev)
+    if n_events is None:
+        n_events = torch.empty(n_traj, dtype=torch.int64, device=dev)
+    if t_final is None:
+        t_final = torch.empty(n_traj, dtype=torch.float64, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().ssa_rdme_run(model.handle, int(nx), int(ny), int(nz), _np_ptr(D), int(n_traj), int(traj_offset),
+                              _np_ptr(x0), float(t_end), K, _np_ptr(st), prec, rnd, int(bool(normalise)),
+                              int(seed) & (2**64 - 1), int(max_events), int(state_bytes), _dev_ptr(out),
+                              _dev_ptr(status), _dev_ptr(n_events), _dev_ptr(t_final), ctypes.c_void_p(s.cuda_stream)))
     return {"snapshots": out, "status": status, "n_events": n_events, "t_final": t_final}
 
 

@@ -173,3 +173,53 @@ def test_tau_run_empty_ensemble_is_a_no_op(ssa):
     rc = ssa.lib().ssa_tau_run(m.handle, 0, 0, x0.ctypes.data, 10.0, 0.5, 1, st.ctypes.data, 0, 0, 0, 0, 4,
                                None, None, None, None, None)
     assert rc == ssa.SSA_OK
+
+
+@pytest.mark.parametrize("case", ["dims", "too_many_voxels", "no_fit", "neg_diffusion", "constant_diffuses",
+                                  "constant_uneven", "sra", "max_events", "neg_x0"])
+def test_rdme_run_rejects_before_launch(ssa, case):
+    """ssa_rdme_run validates on the host before any device call."""
+    m = ssa.Model.from_dict(P.dimer())
+    nx, ny, nz = 4, 2, 1
+    D = np.array([1.0, 0.5])
+    prec, rnd, cap = ssa.PRECISION["fp32"], 0, 1000
+    if case in ("constant_diffuses", "constant_uneven"):
+        m = ssa.Model.from_dict(P.schlogl())
+        D = np.array([1.0, 0.0, 0.0])
+    S = nx * ny * nz
+    x0 = np.ones((S, m.N), np.int32) * 5
+    if case == "dims":
+        nz = 0
+    elif case == "too_many_voxels":
+        nx, ny, nz = 64, 32, 1
+    elif case == "no_fit":
+        nx, ny, nz, prec = 32, 32, 1, ssa.PRECISION["fp64"]
+        x0 = np.ones((1024, m.N), np.int32)
+    elif case == "neg_diffusion":
+        D[0] = -1.0
+    elif case == "constant_diffuses":
+        D[1] = 0.5
+    elif case == "constant_uneven":
+        x0[3, 2] += 1
+    elif case == "sra":
+        prec, rnd = ssa.PRECISION["uniform_f16"], ssa.ROUNDING["sra"]
+    elif case == "max_events":
+        cap = 2**32
+    elif case == "neg_x0":
+        x0[5, 1] = -1
+    st = np.array([0.0, 1.0])
+    fake = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+    rc = ssa.lib().ssa_rdme_run(m.handle, nx, ny, nz, D.ctypes.data, 4, 0, x0.ctypes.data, 1.0, 2, st.ctypes.data,
+                                prec, rnd, 0, 0, cap, 4, fake, fake, None, None, None)
+    assert rc == ssa.SSA_EINVAL, case
+    assert ssa.lib().ssa_last_error()
+
+
+def test_rdme_run_empty_ensemble_is_a_no_op(ssa):
+    m = ssa.Model.from_dict(P.dimer())
+    x0 = np.ones((3, 2), np.int32)
+    D = np.array([1.0, 1.0])
+    st = np.array([1.0])
+    rc = ssa.lib().ssa_rdme_run(m.handle, 3, 1, 1, D.ctypes.data, 0, 0, x0.ctypes.data, 1.0, 1, st.ctypes.data,
+                                0, 0, 0, 0, 100, 4, None, None, None, None, None)
+    assert rc == ssa.SSA_OK

@@ -29,8 +29,12 @@
 //
 // Layout: each lane's counts, tree and epochs sit in dynamic shared memory,
 // interleaved by lane (word index * blockDim + lane), so a warp's
-// data-dependent accesses never conflict on a bank.
+// data-dependent accesses never conflict on a bank.  Compiled structures
+// (the StaticModel families) store only the species that change; reservoir
+// species are read from a block-wide table.  The general model stores all.
 #pragma once
+
+#include <type_traits>
 
 #include "ssa_device.cuh"
 
@@ -41,6 +45,7 @@ constexpr int kMaxVoxels = 1024;
 struct RdmeArgs {
     RunArgs a;                 // structure, c', samples, keys, outputs, queue
     int nx, ny, nz, S, T, depth;
+    int n_stored;              // species stored per voxel (see RdmeSpecies)
     double D[kMaxN];           // hop rate per direction
     const int32_t *x0_lat;     // device [S][N]
 };
@@ -50,22 +55,47 @@ __host__ __device__ inline size_t rdme_align16(size_t v) { return (v + 15) & ~(s
 // Dynamic shared-memory layout of one block: block-wide tables, then the
 // lanes' interleaved columns.
 struct RdmeLayout {
-    size_t smp, consts, nbmask, x, node, epoch, total;
+    size_t smp, consts, cst, nbmask, x, node, epoch, total;
 };
 
-__host__ __device__ inline RdmeLayout rdme_layout(int K, int S, int T, int N, int block, int elem_bytes,
+__host__ __device__ inline RdmeLayout rdme_layout(int K, int S, int T, int n_stored, int block, int elem_bytes,
                                                   bool epochs)
 {
     RdmeLayout L;
     L.smp = 0;
     L.consts = rdme_align16(L.smp + (size_t)K * elem_bytes);
-    L.nbmask = rdme_align16(L.consts + (size_t)(3 * kMaxM + kMaxN) * elem_bytes);
+    L.cst = rdme_align16(L.consts + (size_t)(3 * kMaxM + kMaxN) * elem_bytes);
+    L.nbmask = rdme_align16(L.cst + (size_t)kMaxN * 4);
     L.x = rdme_align16(L.nbmask + (size_t)S);
-    L.node = rdme_align16(L.x + (size_t)S * N * block * 4);
+    L.node = rdme_align16(L.x + (size_t)S * n_stored * block * 4);
     L.epoch = rdme_align16(L.node + (size_t)2 * T * block * elem_bytes);
     L.total = rdme_align16(L.epoch + (epochs ? (size_t)S * block * 4 : 0));
     return L;
 }
+
+// Which species a lattice column holds.  General model: every species, in
+// order.  Compiled structures: the non-constant species, in order.
+template <class Model>
+struct RdmeSpecies {
+    static constexpr bool kStatic = false;
+};
+
+template <class Sx, bool NORM>
+struct RdmeSpecies<StaticModel<Sx, NORM>> {
+    static constexpr bool kStatic = true;
+    __host__ __device__ static constexpr int count()
+    {
+        int c = 0;
+        for (int i = 0; i < Sx::N; ++i) c += Sx::cs[i] ? 0 : 1;
+        return c;
+    }
+    __host__ __device__ static constexpr int slot(int i)
+    {
+        int c = 0;
+        for (int q = 0; q < i; ++q) c += Sx::cs[q] ? 0 : 1;
+        return Sx::cs[i] ? -1 : c;
+    }
+};
 
 // Stochastic-rounding words keyed by (op / 8, epoch, trajectory, tag).
 struct TagBits {
@@ -116,14 +146,28 @@ template <int PREC>
 struct RdmeView {
     using P = typename ModeTraits<PREC>::P;
     const P *smp, *cP, *h0P, *h1P, *DP;
+    const int32_t *cst;    // [N] counts of the constant species (voxel 0)
     const uint8_t *nbmask;
-    int32_t *x;            // &x_columns[lane]; element (v, i) at ((v*N + i) * bd)
+    int32_t *x;            // &x_columns[lane]; stored species s of voxel v at ((v*ns + s) * bd)
     P *node;               // &node_columns[lane]; node q at (q * bd)
     uint32_t *epoch;       // &epoch_columns[lane] or null
-    int bd;
-    __device__ __forceinline__ int32_t &X(int v, int i, int N) const { return x[(v * N + i) * bd]; }
+    int bd, ns;
+    __device__ __forceinline__ int32_t &at(int v, int s) const { return x[(v * ns + s) * bd]; }
     __device__ __forceinline__ P &Node(int q) const { return node[q * bd]; }
 };
+
+// Count of species I (compile time) in voxel v.
+template <class Model, int I, int PREC>
+__device__ __forceinline__ int rdme_get(const RdmeView<PREC> &W, int v)
+{
+    if constexpr (RdmeSpecies<Model>::kStatic) {
+        constexpr int s = RdmeSpecies<Model>::slot(I);
+        if constexpr (s < 0) return W.cst[I];
+        else return W.at(v, s);
+    } else {
+        return W.at(v, I);
+    }
+}
 
 __device__ __forceinline__ int rdme_neighbour(const RdmeArgs &A, int v, int dir)
 {
@@ -137,17 +181,36 @@ __device__ __forceinline__ int rdme_neighbour(const RdmeArgs &A, int v, int dir)
     }
 }
 
+// Partial sums over a voxel's channels with selection (shared by both paths).
+template <int PREC, int SR>
+struct ChannelSum {
+    using Tr = ModeTraits<PREC>;
+    using P = typename Tr::P;
+    VoxelRounder<PREC, SR> *R;
+    int op0;
+    P r, S;
+    int c, mu, last_pos;
+    __device__ __forceinline__ void add(P val)
+    {
+        if (c == 0) S = val;
+        else if constexpr (Tr::kUniform) S = R->rnd(S + val, op0 + c - 1);
+        else S = S + val;
+        if (mu < 0 && S > r) mu = c;
+        if (val > P(0)) last_pos = c;
+        c += 1;
+    }
+};
+
 // Voxel v at epoch e: returns its total; with sel, also the channel selected
 // by residual target r.
-template <int PREC, int SR>
-__device__ __noinline__ typename ModeTraits<PREC>::P rdme_voxel(const RdmeArgs &A, const RdmeView<PREC> &W, int v,
-                                                                uint32_t e, uint32_t traj,
-                                                                typename ModeTraits<PREC>::P r, int *sel)
+template <class Model, int PREC, int SR>
+__device__ __forceinline__ typename ModeTraits<PREC>::P rdme_voxel(const RdmeArgs &A, const RdmeView<PREC> &W, int v,
+                                                                   uint32_t e, uint32_t traj,
+                                                                   typename ModeTraits<PREC>::P r, int *sel)
 {
     using Tr = ModeTraits<PREC>;
     using P = typename Tr::P;
     const RunArgs &a = A.a;
-    const int N = a.N, M = a.M;
     VoxelRounder<PREC, SR> R;
     if constexpr (Tr::k16 && SR) {
         R.bits.e = e;
@@ -157,73 +220,135 @@ __device__ __noinline__ typename ModeTraits<PREC>::P rdme_voxel(const RdmeArgs &
         R.bits.k1 = a.key1;
         R.bits.cur = -1;
     }
-    P prop[kMaxM];
-#pragma unroll 1
-    for (int j = 0; j < M; ++j) {
-        int op = a.chain_start[j];
-        if (a.law[j] == 1) {
-            const P Pv = R.rnd((P)W.X(v, a.hill_reg[j], N), op++);
-            P q = Pv;
-            for (int m = 1; m < a.hill_h[j]; ++m) q = R.rnd(q * Pv, op++);
-            const P d = R.rnd(P(1) + q, op++);
-            const P f = R.rnd(W.h1P[j] / d, op++);
-            prop[j] = R.rnd(W.h0P[j] + f, op++);
-        } else {
-            P av = W.cP[j];
-            bool zero = false;
-#pragma unroll 1
-            for (int i = 0; i < N; ++i) {
-                const int rr = a.order[j][i];
-                if (rr == 0 || a.folded[j][i]) continue;
-                const int xi = W.X(v, i, N);
-                zero = zero || (xi < rr);
-                for (int m = 0; m < rr; ++m) {
-                    const P f = R.rnd((P)(xi - m), op++);
-                    av = R.rnd(av * f, op++);
-                }
-            }
-            prop[j] = zero ? P(0) : av;
-        }
-    }
     const uint8_t nb = W.nbmask[v];
     const int nnb = __popc((unsigned)nb);
-    P hv[kMaxN];
-    int op = a.sr_ops;
-#pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-        hv[i] = P(0);
-        if (nnb == 0 || !(A.D[i] > 0.0)) continue;
-        const int xi = W.X(v, i, N);
-        if (xi < 1) {
-            op += 2;
-        } else {
-            const P f = R.rnd((P)xi, op++);
-            hv[i] = R.rnd(W.DP[i] * f, op++);
+    ChannelSum<PREC, SR> cs;
+    cs.R = &R;
+    cs.r = r;
+    cs.S = P(0);
+    cs.c = 0;
+    cs.mu = -1;
+    cs.last_pos = -1;
+
+    if constexpr (RdmeSpecies<Model>::kStatic) {
+        constexpr int M = Model::M, N = Model::N;
+        P prop[M];
+        unroll<M>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            int op = Model::template chain_start<j>(a);
+            if (Model::template law<j>(a) == 1) {
+                const int reg = Model::template hill_reg<j>(a);
+                int xr = 0;
+                unroll<N>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    if (i == reg) xr = rdme_get<Model, i>(W, v);
+                });
+                const P Pv = R.rnd((P)xr, op++);
+                P q = Pv;
+                const int h = Model::template hill_h<j>(a);
+                for (int m = 1; m < h; ++m) q = R.rnd(q * Pv, op++);
+                const P d = R.rnd(P(1) + q, op++);
+                const P f = R.rnd(W.h1P[j] / d, op++);
+                prop[j] = R.rnd(W.h0P[j] + f, op++);
+            } else {
+                P av = W.cP[j];
+                bool zero = false;
+                unroll<N>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    const int rr = Model::template order<j, i>(a);
+                    if (rr > 0 && !Model::template folded<j, i>(a)) {
+                        const int xi = rdme_get<Model, i>(W, v);
+                        zero = zero || (xi < rr);
+                        for (int m = 0; m < rr; ++m) {
+                            const P f = R.rnd((P)(xi - m), op++);
+                            av = R.rnd(av * f, op++);
+                        }
+                    }
+                });
+                prop[j] = zero ? P(0) : av;
+            }
+        });
+        P hv[N];
+        int op = Model::total_chain_ops(a);
+        unroll<N>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            hv[i] = P(0);
+            if (nnb > 0 && A.D[i] > 0.0) {
+                const int xi = rdme_get<Model, i>(W, v);
+                if (xi < 1) {
+                    op += 2;
+                } else {
+                    const P f = R.rnd((P)xi, op++);
+                    hv[i] = R.rnd(W.DP[i] * f, op++);
+                }
+            }
+        });
+        cs.op0 = op;
+        unroll<M>([&](auto J) { cs.add(prop[decltype(J)::value]); });
+        if (nnb > 0) {
+            unroll<N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                if (A.D[i] > 0.0)
+                    for (int d = 0; d < nnb; ++d) cs.add(hv[i]);
+            });
         }
-    }
-    // partial sums over reactions, then hops (one per species and direction)
-    const int sum_op0 = op;
-    P S = P(0);
-    int c = 0, mu = -1, last_pos = -1;
-    auto add = [&](P val) {
-        if (c == 0) S = val;
-        else if constexpr (Tr::kUniform) S = R.rnd(S + val, sum_op0 + c - 1);
-        else S = S + val;
-        if (mu < 0 && S > r) mu = c;
-        if (val > P(0)) last_pos = c;
-        c += 1;
-    };
+    } else {
+        const int N = a.N, M = a.M;
+        P prop[kMaxM];
 #pragma unroll 1
-    for (int j = 0; j < M; ++j) add(prop[j]);
-    if (nnb > 0) {
+        for (int j = 0; j < M; ++j) {
+            int op = a.chain_start[j];
+            if (a.law[j] == 1) {
+                const P Pv = R.rnd((P)W.at(v, a.hill_reg[j]), op++);
+                P q = Pv;
+                for (int m = 1; m < a.hill_h[j]; ++m) q = R.rnd(q * Pv, op++);
+                const P d = R.rnd(P(1) + q, op++);
+                const P f = R.rnd(W.h1P[j] / d, op++);
+                prop[j] = R.rnd(W.h0P[j] + f, op++);
+            } else {
+                P av = W.cP[j];
+                bool zero = false;
+#pragma unroll 1
+                for (int i = 0; i < N; ++i) {
+                    const int rr = a.order[j][i];
+                    if (rr == 0 || a.folded[j][i]) continue;
+                    const int xi = W.at(v, i);
+                    zero = zero || (xi < rr);
+                    for (int m = 0; m < rr; ++m) {
+                        const P f = R.rnd((P)(xi - m), op++);
+                        av = R.rnd(av * f, op++);
+                    }
+                }
+                prop[j] = zero ? P(0) : av;
+            }
+        }
+        P hv[kMaxN];
+        int op = a.sr_ops;
 #pragma unroll 1
         for (int i = 0; i < N; ++i) {
-            if (!(A.D[i] > 0.0)) continue;
-            for (int d = 0; d < nnb; ++d) add(hv[i]);
+            hv[i] = P(0);
+            if (nnb == 0 || !(A.D[i] > 0.0)) continue;
+            const int xi = W.at(v, i);
+            if (xi < 1) {
+                op += 2;
+            } else {
+                const P f = R.rnd((P)xi, op++);
+                hv[i] = R.rnd(W.DP[i] * f, op++);
+            }
+        }
+        cs.op0 = op;
+#pragma unroll 1
+        for (int j = 0; j < M; ++j) cs.add(prop[j]);
+        if (nnb > 0) {
+#pragma unroll 1
+            for (int i = 0; i < N; ++i) {
+                if (!(A.D[i] > 0.0)) continue;
+                for (int d = 0; d < nnb; ++d) cs.add(hv[i]);
+            }
         }
     }
-    if (sel) *sel = mu >= 0 ? mu : last_pos;
-    return S;
+    if (sel) *sel = cs.mu >= 0 ? cs.mu : cs.last_pos;
+    return cs.S;
 }
 
 template <int PREC, int SR>
@@ -245,32 +370,42 @@ __device__ __forceinline__ typename ModeTraits<PREC>::P rdme_node(const RdmeArgs
     }
 }
 
-template <int PREC>
+__device__ __forceinline__ void rdme_put(const RunArgs &a, int64_t idx, int val, uint32_t &status)
+{
+    if (a.state_bytes == 2) {
+        if (val > 32767) { val = 32767; status |= ST_STATE_RANGE; }
+        if (val < -32768) { val = -32768; status |= ST_STATE_RANGE; }
+        static_cast<int16_t *>(a.out)[idx] = (int16_t)val;
+    } else {
+        static_cast<int32_t *>(a.out)[idx] = val;
+    }
+}
+
+template <class Model, int PREC>
 __device__ void rdme_store(const RdmeArgs &A, const RdmeView<PREC> &W, int k, int64_t item, uint32_t &status)
 {
     const RunArgs &a = A.a;
     const int N = a.N;
 #pragma unroll 1
-    for (int v = 0; v < A.S; ++v)
+    for (int v = 0; v < A.S; ++v) {
+        const int64_t base = ((int64_t)k * A.S + v) * N;
+        if constexpr (RdmeSpecies<Model>::kStatic) {
+            unroll<Model::N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                rdme_put(a, (base + i) * a.n_traj + item, rdme_get<Model, i>(W, v), status);
+            });
+        } else {
 #pragma unroll 1
-        for (int i = 0; i < N; ++i) {
-            const int64_t idx = (((int64_t)k * A.S + v) * N + i) * a.n_traj + item;
-            int val = W.X(v, i, N);
-            if (a.state_bytes == 2) {
-                if (val > 32767) { val = 32767; status |= ST_STATE_RANGE; }
-                if (val < -32768) { val = -32768; status |= ST_STATE_RANGE; }
-                static_cast<int16_t *>(a.out)[idx] = (int16_t)val;
-            } else {
-                static_cast<int32_t *>(a.out)[idx] = val;
-            }
+            for (int i = 0; i < N; ++i) rdme_put(a, (base + i) * a.n_traj + item, W.at(v, i), status);
         }
+    }
 }
 
-template <int PREC>
+template <class Model, int PREC>
 __device__ void rdme_finish(const RdmeArgs &A, const RdmeView<PREC> &W, RLane<PREC> &L)
 {
     while (L.k < A.a.K) {
-        rdme_store<PREC>(A, W, L.k, L.item, L.status);
+        rdme_store<Model, PREC>(A, W, L.k, L.item, L.status);
         L.k += 1;
     }
     A.a.status[L.item] = L.status;
@@ -279,7 +414,7 @@ __device__ void rdme_finish(const RdmeArgs &A, const RdmeView<PREC> &W, RLane<PR
     L.active = false;
 }
 
-template <int PREC, int SR>
+template <class Model, int PREC, int SR>
 __device__ void rdme_init(const RdmeArgs &A, const RdmeView<PREC> &W, RLane<PREC> &L, int64_t item)
 {
     using P = typename ModeTraits<PREC>::P;
@@ -287,12 +422,21 @@ __device__ void rdme_init(const RdmeArgs &A, const RdmeView<PREC> &W, RLane<PREC
     L.item = item;
     L.traj = A.a.traj_offset + (uint32_t)item;
 #pragma unroll 1
-    for (int v = 0; v < A.S; ++v)
+    for (int v = 0; v < A.S; ++v) {
+        if constexpr (RdmeSpecies<Model>::kStatic) {
+            unroll<Model::N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int s = RdmeSpecies<Model>::slot(i);
+                if constexpr (s >= 0) W.at(v, s) = A.x0_lat[v * N + i];
+            });
+        } else {
 #pragma unroll 1
-        for (int i = 0; i < N; ++i) W.X(v, i, N) = A.x0_lat[v * N + i];
+            for (int i = 0; i < N; ++i) W.at(v, i) = A.x0_lat[v * N + i];
+        }
+    }
 #pragma unroll 1
     for (int v = 0; v < A.T; ++v) {
-        W.Node(A.T + v) = v < A.S ? rdme_voxel<PREC, SR>(A, W, v, 0u, L.traj, P(0), nullptr) : P(0);
+        W.Node(A.T + v) = v < A.S ? rdme_voxel<Model, PREC, SR>(A, W, v, 0u, L.traj, P(0), nullptr) : P(0);
         if (W.epoch && v < A.S) W.epoch[v * W.bd] = 0u;
     }
 #pragma unroll 1
@@ -305,26 +449,106 @@ __device__ void rdme_init(const RdmeArgs &A, const RdmeView<PREC> &W, RLane<PREC
     L.active = true;
 }
 
+// Apply channel c of voxel v; returns the hop's destination voxel or -1.
+template <class Model, int PREC>
+__device__ __forceinline__ int rdme_apply(const RdmeArgs &A, const RdmeView<PREC> &W, int v, int c, bool &negative)
+{
+    const RunArgs &a = A.a;
+    negative = false;
+    if (c < a.M) {
+        if constexpr (RdmeSpecies<Model>::kStatic) {
+            unroll<Model::N>([&](auto I) {      // branch-free: d_i = nu[c][i] by selects
+                constexpr int i = decltype(I)::value;
+                constexpr int s = RdmeSpecies<Model>::slot(i);
+                if constexpr (s >= 0) {
+                    int d = 0;
+                    bool moves = false;
+                    unroll<Model::M>([&](auto J) {
+                        constexpr int j = decltype(J)::value;
+                        const int nu = Model::template nu<j, i>(a);
+                        if (nu != 0) {
+                            d = (c == j) ? nu : d;
+                            moves = true;
+                        }
+                    });
+                    if (moves) {
+                        int &xr = W.at(v, s);
+                        xr += d;
+                        negative = negative || (xr < 0);
+                    }
+                }
+            });
+        } else {
+#pragma unroll 1
+            for (int i = 0; i < a.N; ++i) {
+                const int d = a.stoich[c][i];
+                if (d == 0) continue;
+                int &xr = W.at(v, i);
+                xr += d;
+                negative = negative || (xr < 0);
+            }
+        }
+        return -1;
+    }
+    int idx = c - a.M, species = -1, dir = -1;
+    const uint8_t nb = W.nbmask[v];
+    const int nnb = __popc((unsigned)nb);
+#pragma unroll 1
+    for (int i = 0; i < a.N && species < 0; ++i) {
+        if (!(A.D[i] > 0.0)) continue;
+        if (idx < nnb) {
+            species = i;
+            int seen = 0;
+            for (int d = 0; d < 6; ++d) {
+                if (!((nb >> d) & 1u)) continue;
+                if (seen == idx) { dir = d; break; }
+                seen += 1;
+            }
+        } else {
+            idx -= nnb;
+        }
+    }
+    const int w = rdme_neighbour(A, v, dir);
+    if constexpr (RdmeSpecies<Model>::kStatic) {
+        unroll<Model::N>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int s = RdmeSpecies<Model>::slot(i);
+            if constexpr (s >= 0) {
+                if (i == species) {
+                    W.at(v, s) -= 1;
+                    W.at(w, s) += 1;
+                    negative = W.at(v, s) < 0;
+                }
+            }
+        });
+    } else {
+        W.at(v, species) -= 1;
+        W.at(w, species) += 1;
+        negative = W.at(v, species) < 0;
+    }
+    return w;
+}
+
 // One event of an active lane (contract above).
-template <int PREC, int SR>
-__device__ __noinline__ void rdme_event(const RdmeArgs &A, const RdmeView<PREC> &W, RLane<PREC> &L,
-                                        typename ModeTraits<PREC>::P t_end)
+template <class Model, int PREC, int SR>
+__device__ __forceinline__ void rdme_event(const RdmeArgs &A, const RdmeView<PREC> &W, RLane<PREC> &L,
+                                           typename ModeTraits<PREC>::P t_end)
 {
     using Tr = ModeTraits<PREC>;
     using P = typename Tr::P;
     const RunArgs &a = A.a;
     const P kInf = P(__int_as_float(0x7F800000));
-    const int N = a.N, T = A.T;
+    const int T = A.T;
 
     if (L.n >= a.max_events) {
         L.status |= ST_MAX_EVENTS;
-        rdme_finish<PREC>(A, W, L);
+        rdme_finish<Model, PREC>(A, W, L);
         return;
     }
     const P a0 = W.Node(1);
-    if (a0 != a0) { L.status |= ST_NAN; rdme_finish<PREC>(A, W, L); return; }
-    if (a0 == kInf) { L.status |= ST_OVERFLOW; rdme_finish<PREC>(A, W, L); return; }
-    if (a0 == P(0)) { rdme_finish<PREC>(A, W, L); return; }
+    if (a0 != a0) { L.status |= ST_NAN; rdme_finish<Model, PREC>(A, W, L); return; }
+    if (a0 == kInf) { L.status |= ST_OVERFLOW; rdme_finish<Model, PREC>(A, W, L); return; }
+    if (a0 == P(0)) { rdme_finish<Model, PREC>(A, W, L); return; }
 
     if ((L.n & 1) == 0) {
         const uint64_t blk = (uint64_t)L.n >> 1;
@@ -366,11 +590,11 @@ __device__ __noinline__ void rdme_event(const RdmeArgs &A, const RdmeView<PREC> 
         }
     }
     while (L.s_next < t_new) {
-        rdme_store<PREC>(A, W, L.k, L.item, L.status);
+        rdme_store<Model, PREC>(A, W, L.k, L.item, L.status);
         L.k += 1;
         L.s_next = L.k < a.K ? W.smp[L.k] : kInf;
     }
-    if (t_new > t_end) { rdme_finish<PREC>(A, W, L); return; }
+    if (t_new > t_end) { rdme_finish<Model, PREC>(A, W, L); return; }
 
     // voxel by descent of the sum tree
     int q = 1, level = 0;
@@ -392,62 +616,27 @@ __device__ __noinline__ void rdme_event(const RdmeArgs &A, const RdmeView<PREC> 
     const int v = q - T;
     const uint32_t ev = W.epoch ? W.epoch[v * W.bd] : 0u;
     int c = -1;
-    rdme_voxel<PREC, SR>(A, W, v, ev, L.traj, r, &c);
+    rdme_voxel<Model, PREC, SR>(A, W, v, ev, L.traj, r, &c);
     if (c < 0) {            // unreachable (the descent enters only positive totals); kept as a guard
         L.status |= ST_NAN;
-        rdme_finish<PREC>(A, W, L);
+        rdme_finish<Model, PREC>(A, W, L);
         return;
     }
-
-    // apply: a reaction of voxel v, or a hop v -> w
-    int w = -1;
     bool negative = false;
-    if (c < a.M) {
-#pragma unroll 1
-        for (int i = 0; i < N; ++i) {
-            const int d = a.stoich[c][i];
-            if (d == 0) continue;
-            int &xr = W.X(v, i, N);
-            xr += d;
-            negative = negative || (xr < 0);
-        }
-    } else {
-        int idx = c - a.M, species = -1, dir = -1;
-        const uint8_t nb = W.nbmask[v];
-        const int nnb = __popc((unsigned)nb);
-#pragma unroll 1
-        for (int i = 0; i < N && species < 0; ++i) {
-            if (!(A.D[i] > 0.0)) continue;
-            if (idx < nnb) {
-                species = i;
-                int seen = 0;
-                for (int d = 0; d < 6; ++d) {
-                    if (!((nb >> d) & 1u)) continue;
-                    if (seen == idx) { dir = d; break; }
-                    seen += 1;
-                }
-            } else {
-                idx -= nnb;
-            }
-        }
-        w = rdme_neighbour(A, v, dir);
-        W.X(v, species, N) -= 1;
-        W.X(w, species, N) += 1;
-        negative = W.X(v, species, N) < 0;
-    }
+    const int w = rdme_apply<Model, PREC>(A, W, v, c, negative);
     L.t = t_new;
     L.n += 1;
     if (negative) {
         L.status |= ST_STATE_RANGE;
-        rdme_finish<PREC>(A, W, L);
+        rdme_finish<Model, PREC>(A, W, L);
         return;
     }
     // recompute the changed voxels and their ancestors at epoch n + 1
     const uint32_t e = (uint32_t)L.n;
-    W.Node(T + v) = rdme_voxel<PREC, SR>(A, W, v, e, L.traj, P(0), nullptr);
+    W.Node(T + v) = rdme_voxel<Model, PREC, SR>(A, W, v, e, L.traj, P(0), nullptr);
     if (W.epoch) W.epoch[v * W.bd] = e;
     if (w >= 0) {
-        W.Node(T + w) = rdme_voxel<PREC, SR>(A, W, w, e, L.traj, P(0), nullptr);
+        W.Node(T + w) = rdme_voxel<Model, PREC, SR>(A, W, w, e, L.traj, P(0), nullptr);
         if (W.epoch) W.epoch[w * W.bd] = e;
     }
     int qa = (T + v) >> 1, qb = w >= 0 ? (T + w) >> 1 : 0;
@@ -463,7 +652,7 @@ __device__ __noinline__ void rdme_event(const RdmeArgs &A, const RdmeView<PREC> 
 
 // Persistent RDME kernel: lanes refill from the work queue; each loop
 // iteration runs one event.
-template <int PREC, int SR>
+template <class Model, int PREC, int SR>
 __global__ void __launch_bounds__(256) rdme_kernel(const __grid_constant__ RdmeArgs A)
 {
     using Tr = ModeTraits<PREC>;
@@ -472,9 +661,10 @@ __global__ void __launch_bounds__(256) rdme_kernel(const __grid_constant__ RdmeA
     const int bd = blockDim.x, tid = threadIdx.x;
     const RunArgs &a = A.a;
     constexpr bool kEpochs = Tr::k16 && SR != 0;
-    const RdmeLayout lay = rdme_layout(a.K, A.S, A.T, a.N, bd, (int)sizeof(P), kEpochs);
+    const RdmeLayout lay = rdme_layout(a.K, A.S, A.T, A.n_stored, bd, (int)sizeof(P), kEpochs);
     P *smp = reinterpret_cast<P *>(rdme_smem + lay.smp);
     P *cons = reinterpret_cast<P *>(rdme_smem + lay.consts);
+    int32_t *cst = reinterpret_cast<int32_t *>(rdme_smem + lay.cst);
     uint8_t *nbm = rdme_smem + lay.nbmask;
     for (int k = tid; k < a.K; k += bd) smp[k] = to_time<PREC>(a.samples[k]);
     for (int j = tid; j < kMaxM; j += bd) {
@@ -483,7 +673,10 @@ __global__ void __launch_bounds__(256) rdme_kernel(const __grid_constant__ RdmeA
         cons[kMaxM + j] = on && a.law[j] == 1 ? to_prop<PREC>(a.hill_a0[j]) : P(0);
         cons[2 * kMaxM + j] = on && a.law[j] == 1 ? to_prop<PREC>(a.hill_a[j]) : P(0);
     }
-    for (int i = tid; i < kMaxN; i += bd) cons[3 * kMaxM + i] = i < a.N ? to_prop<PREC>(A.D[i]) : P(0);
+    for (int i = tid; i < kMaxN; i += bd) {
+        cons[3 * kMaxM + i] = i < a.N ? to_prop<PREC>(A.D[i]) : P(0);
+        cst[i] = i < a.N ? A.x0_lat[i] : 0;
+    }
     for (int v = tid; v < A.S; v += bd) {
         const int ix = v % A.nx, iy = (v / A.nx) % A.ny, iz = v / (A.nx * A.ny);
         uint8_t m = 0;
@@ -503,11 +696,13 @@ __global__ void __launch_bounds__(256) rdme_kernel(const __grid_constant__ RdmeA
     W.h0P = cons + kMaxM;
     W.h1P = cons + 2 * kMaxM;
     W.DP = cons + 3 * kMaxM;
+    W.cst = cst;
     W.nbmask = nbm;
     W.x = reinterpret_cast<int32_t *>(rdme_smem + lay.x) + tid;
     W.node = reinterpret_cast<P *>(rdme_smem + lay.node) + tid;
     W.epoch = kEpochs ? reinterpret_cast<uint32_t *>(rdme_smem + lay.epoch) + tid : nullptr;
     W.bd = bd;
+    W.ns = A.n_stored;
     const P t_end = to_time<PREC>(a.t_end);
 
     const unsigned lane = threadIdx.x & 31u;
@@ -523,12 +718,77 @@ __global__ void __launch_bounds__(256) rdme_kernel(const __grid_constant__ RdmeA
             base = __shfl_sync(0xFFFFFFFFu, base, leader);
             if (!L.active && !drained) {
                 const unsigned long long item = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-                if (item < (unsigned long long)a.n_work) rdme_init<PREC, SR>(A, W, L, (int64_t)item);
+                if (item < (unsigned long long)a.n_work) rdme_init<Model, PREC, SR>(A, W, L, (int64_t)item);
                 else drained = true;
             }
         }
         if (__ballot_sync(0xFFFFFFFFu, L.active) == 0u) break;
-        if (L.active) rdme_event<PREC, SR>(A, W, L, t_end);
+        if (L.active) rdme_event<Model, PREC, SR>(A, W, L, t_end);
+    }
+}
+
+// Threads per block: the largest multiple of 32 (at most max_block) whose
+// columns fit in the opt-in shared memory of one block; 0 if none does.
+inline int rdme_block_size_for(const RdmeArgs &A, int elem_bytes, bool epochs, int max_block, size_t smem_limit)
+{
+    int block = (max_block / 32) * 32;
+    while (block >= 32 && rdme_layout(A.a.K, A.S, A.T, A.n_stored, block, elem_bytes, epochs).total > smem_limit)
+        block -= 32;
+    return block < 32 ? 0 : block;
+}
+
+template <class Model, int PREC, int SR>
+cudaError_t rdme_launch_mode(const RdmeArgs &A, int max_block, int blocks_per_sm, size_t smem_limit,
+                             cudaStream_t stream, int *grid_out, int *block_out)
+{
+    using P = typename ModeTraits<PREC>::P;
+    constexpr bool kEpochs = ModeTraits<PREC>::k16 && SR != 0;
+    auto k = rdme_kernel<Model, PREC, SR>;
+    const int block = rdme_block_size_for(A, (int)sizeof(P), kEpochs, max_block, smem_limit);
+    if (block < 32) return cudaErrorInvalidConfiguration;
+    const size_t bytes = rdme_layout(A.a.K, A.S, A.T, A.n_stored, block, (int)sizeof(P), kEpochs).total;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+    long long grid = (long long)sms * per_sm;
+    const long long need = (A.a.n_work + block - 1) / block;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    *grid_out = (int)grid;
+    *block_out = block;
+    k<<<(unsigned)grid, (unsigned)block, bytes, stream>>>(A);
+    return cudaGetLastError();
+}
+
+// All (precision, rounding) instantiations of one model structure.
+template <class Model>
+cudaError_t rdme_launch_model(const RdmeArgs &A, int prec, int sr, int max_block, int blocks_per_sm,
+                              size_t smem_limit, cudaStream_t s, int *grid, int *block)
+{
+    switch (prec) {
+    case FP64: return rdme_launch_mode<Model, FP64, 0>(A, max_block, blocks_per_sm, smem_limit, s, grid, block);
+    case FP32: return rdme_launch_mode<Model, FP32, 0>(A, max_block, blocks_per_sm, smem_limit, s, grid, block);
+    case MIXED_F16:
+        return sr ? rdme_launch_mode<Model, MIXED_F16, 1>(A, max_block, blocks_per_sm, smem_limit, s, grid, block)
+                  : rdme_launch_mode<Model, MIXED_F16, 0>(A, max_block, blocks_per_sm, smem_limit, s, grid, block);
+    case MIXED_BF16:
+        return sr ? rdme_launch_mode<Model, MIXED_BF16, 1>(A, max_block, blocks_per_sm, smem_limit, s, grid, block)
+                  : rdme_launch_mode<Model, MIXED_BF16, 0>(A, max_block, blocks_per_sm, smem_limit, s, grid, block);
+    case UNIFORM_F16:
+        return sr ? rdme_launch_mode<Model, UNIFORM_F16, 1>(A, max_block, blocks_per_sm, smem_limit, s, grid, block)
+                  : rdme_launch_mode<Model, UNIFORM_F16, 0>(A, max_block, blocks_per_sm, smem_limit, s, grid, block);
+    case UNIFORM_BF16:
+        return sr ? rdme_launch_mode<Model, UNIFORM_BF16, 1>(A, max_block, blocks_per_sm, smem_limit, s, grid, block)
+                  : rdme_launch_mode<Model, UNIFORM_BF16, 0>(A, max_block, blocks_per_sm, smem_limit, s, grid, block);
+    default: return cudaErrorInvalidValue;
     }
 }
 

@@ -413,6 +413,11 @@ int ssa_rdme_run(const ssa_model *model, int nx, int ny, int nz, const double *d
         A->depth += 1;
     }
     for (int i = 0; i < N; ++i) A->D[i] = diffusion[i];
+    A->n_stored = N;                      // general model: every species
+    if (model->family != 0) {             // compiled structures keep reservoirs out of the lattice
+        A->n_stored = 0;
+        for (int i = 0; i < N; ++i) A->n_stored += model->constant[i] ? 0 : 1;
+    }
     A->a.K = n_samples;
     A->a.n_traj = n_traj;
     A->a.n_work = n_traj;
@@ -459,7 +464,7 @@ int ssa_rdme_run(const ssa_model *model, int nx, int ny, int nz, const double *d
         return cuda_fail(e, "RDME table upload");
     }
     int grid = 0, block = 0;
-    e = ssa::launch_rdme(*A, precision, rounding, g_cfg, s, &grid, &block);
+    e = ssa::launch_rdme(*A, model->family, normalise ? 1 : 0, precision, rounding, g_cfg, s, &grid, &block);
     cudaError_t e2 = cudaFreeAsync(d, s);
     delete A;
     if (e != cudaSuccess) return cuda_fail(e, "RDME kernel launch");

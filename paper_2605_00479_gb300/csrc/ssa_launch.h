@@ -31,13 +31,15 @@ cudaError_t launch_repressilator(const RunArgs &, int, int, int, LaunchConfig, c
 // 1 SR), leap a.tau, a.n_leaps leaps.
 cudaError_t launch_tau(const RunArgs &a, int prec, int sr, LaunchConfig cfg, cudaStream_t stream, int *grid_out);
 
-// RDME kernel (ssa_k_rdme.cu).  Threads per block are the largest multiple of
-// 32 (at most max_block) whose lattice columns fit in shared memory; 0 if not
-// even one warp fits.  launch_rdme writes the grid and block it used.
+// RDME kernels (ssa_k_rdme*.cu).  rdme_block_size: threads per block, the
+// largest multiple of 32 (at most max_block) whose lattice columns fit in
+// shared memory, 0 if not even one warp fits.  launch_rdme picks the compiled
+// structure `family` (0 = general; norm selects the folded Schloegl variant)
+// and writes the grid and block it used.
 struct RdmeArgs;
 int rdme_block_size(const RdmeArgs &A, int elem_bytes, bool epochs, int max_block);
-cudaError_t launch_rdme(const RdmeArgs &A, int prec, int sr, LaunchConfig cfg, cudaStream_t stream, int *grid_out,
-                        int *block_out);
+cudaError_t launch_rdme(const RdmeArgs &A, int family, int norm, int prec, int sr, LaunchConfig cfg,
+                        cudaStream_t stream, int *grid_out, int *block_out);
 
 // Shared launch logic: choose the kernel for (prec, sr), size the grid from
 // occupancy (persistent: enough lanes to fill the GPU, no more than the work).

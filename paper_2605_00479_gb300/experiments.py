@@ -6,7 +6,7 @@
     python -m paper_2605_00479_gb300.experiments sweeps
     python -m paper_2605_00479_gb300.experiments dwell
     python -m paper_2605_00479_gb300.experiments tau    [n_traj=200000]
-    python -m paper_2605_00479_gb300.experiments rdme   [n_traj=16384] [fp64_traj=2048]
+    python -m paper_2605_00479_gb300.experiments rdme   [n_traj=131072] [fp64_traj=8192]
 
 batch: telegraph (kon, koff log-uniform in [0.05, 5], km in [5, 100], gamma 1),
   dimerisation (k1, k2 log-uniform in [x0.5, x2] around 1e-3, 0.1; M0 = 300)
@@ -44,10 +44,11 @@ tau: fixed-leap tau-leaping in reduced precision (the combination the paper
   fp16.
 rdme: spatial Schloegl chain -- 32 voxels in a line, each the bistable Schloegl
   system (reservoirs folded, X0 = 250), X hopping to each neighbour at rate
-  D = 1 per molecule, reflecting ends, t_end = 10, one snapshot at t_end.
+  D = 1 per molecule, reflecting ends, t_end = 2, one snapshot at t_end;
+  2^17 trajectories (two per lane of a full GPU at this lattice's footprint).
   Every mode's pooled voxel counts against the fp64 ensemble (KS p, W1, mean,
   variance), the neighbour covariance of X, overflow fraction and events/s
-  (reactions + hops); at most 8e6 events per trajectory.
+  (reactions + hops); at most 4e6 events per trajectory.
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -307,14 +308,14 @@ def tau(n_traj=200000, seed=41):
     return out
 
 
-def rdme(n_traj=16384, fp64_traj=2048, seed=51):
+def rdme(n_traj=131072, fp64_traj=8192, seed=51):
     import torch
     md = P.schlogl()
     S = 32
     x0 = np.tile(P.schlogl_x0(md), (S, 1)).astype(np.int32)
     D = [1.0, 0.0, 0.0]
-    t_end = 10.0
-    cap = 8 * 10**6          # events per trajectory (about 1.6e6 expected); bounds stagnating clocks
+    t_end = 2.0
+    cap = 4 * 10**6          # events per trajectory (about 4e5 expected); bounds stagnating clocks
     m = ssa.Model.from_dict(md)
     out = {"lattice": [S, 1, 1], "max_events": cap, "diffusion": D, "t_end": t_end, "n_traj": n_traj, "fp64_traj": fp64_traj,
            "note": "X pooled over voxels at t_end vs the fp64 ensemble (different seed)", "modes": {}}

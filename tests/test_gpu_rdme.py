@@ -32,6 +32,17 @@ def inert():
     return {"order": np.zeros((1, 1), np.int32), "stoich": np.zeros((1, 1), np.int32), "rate": np.array([0.0])}
 
 
+def general_network():
+    """Species (X, Y, Z) with Z a reservoir; orders up to 3; no compiled structure."""
+    return {
+        "order": np.array([[1, 0, 1], [2, 0, 0], [0, 1, 0], [0, 3, 0], [0, 0, 0], [1, 0, 0]], np.int32),
+        "stoich": np.array([[1, 0, -1], [-2, 1, 0], [1, -1, 0], [0, -3, 0], [0, 1, 0], [-1, 0, 0]], np.int32),
+        "rate": np.array([0.02, 0.01, 0.5, 0.001, 2.0, 0.1]),
+        "law": np.zeros(6, np.int32),
+        "constant": np.array([0, 0, 1], np.uint8),
+    }
+
+
 def point_source(S, N, counts):
     x0 = np.zeros((S, N), np.int32)
     x0[0] = counts
@@ -56,6 +67,10 @@ CASES = {
                       P.even_samples(0.5, 3), True, 60000),
     "repressilator_pair": (P.repressilator(), (2,), [0.5, 0.5, 0.5, 0.1, 0.1, 0.1],
                            np.tile(P.REPRESSILATOR_X0, (2, 1)), 60, 2.0, P.even_samples(2.0, 3), False, 60000),
+    "schlogl_chain_raw": (*schlogl_chain()[:1], (4,), [2.0, 0.0, 0.0], schlogl_chain()[1], 32, 0.2,
+                          P.even_samples(0.2, 3), False, 30000),
+    "general_reservoir": (general_network(), (2, 2), [0.3, 0.6, 0.0], np.tile([10, 5, 50], (4, 1)), 200, 5.0,
+                          P.even_samples(5.0, 4), True, 20000),
     "single_voxel": (P.dimer(), (1,), [1.0, 1.0], P.dimer_x0(300)[None, :], 200, 10.0, P.even_samples(10.0, 5),
                      False, 10**6),
 }

@@ -11,6 +11,9 @@ independent, so N GPUs run N disjoint trajectory-id ranges (weak scaling, no
 collective on the data path).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                      [--workload schlogl|tau|rdme]
+(--workload tau / rdme: the tau-leaping and RDME extensions, same contract;
+see the section above run_ext.)
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
@@ -247,7 +250,7 @@ def config_block():
 # ------------------------------------------------------------- our arm
 def run_ours(args, world, rank, local):
     import torch
-    from oracle import stats
+    from scipy import stats as sst
     from paper_2605_00479_gb300 import ssa
 
     torch.cuda.set_device(local)
@@ -396,14 +399,15 @@ def run_ours(args, world, rank, local):
     for (prec, rnd), vals in rec.items():
         xs = vals[-1][1].cpu().numpy()
         st = vals[-1][2].cpu().numpy()
-        D, p = stats.ks_2samp(ref, xs)
-        D4, p4 = stats.ks_2samp(ref[:10000], xs[:10000])
+        D, p = sst.ks_2samp(ref, xs)
+        D4, p4 = sst.ks_2samp(ref[:10000], xs[:10000])
         ev_alone = float(rec_alone[(prec, rnd)][0][0])
         rate = ev_alone / (alone_ms[(prec, rnd)] / 1e3)
         modes_out[f"{prec}:{rnd}"] = {
             "events_per_s": rate, "ms_per_launch_alone": alone_ms[(prec, rnd)],
             "ms_per_launch_in_step": float(np.mean(kernel_ms[(prec, rnd)])), "speedup_vs_fp64": rate / fp64_rate,
-            "ks_p_vs_fp64": p, "ks_p_vs_fp64_n1e4": p4, "w1_vs_fp64": stats.wasserstein1(ref, xs),
+            "ks_p_vs_fp64": float(p), "ks_p_vs_fp64_n1e4": float(p4),
+            "w1_vs_fp64": float(sst.wasserstein_distance(ref, xs)),
             "mean": float(xs.mean()), "var": float(xs.var()), "frac_max_events": float(np.mean((st & 2) != 0)),
             "ops_per_event": ops_per_event(prec, rnd)}
     for prec, rnd in EXTRA_MODES:
@@ -413,8 +417,9 @@ def run_ours(args, world, rank, local):
         rate = ev_alone / (alone_ms[(prec, rnd)] / 1e3)
         modes_out[f"{prec}:{rnd}"] = {
             "events_per_s": rate, "ms_per_launch_alone": alone_ms[(prec, rnd)], "in_step": False,
-            "speedup_vs_fp64": rate / fp64_rate, "ks_p_vs_fp64": stats.ks_2samp(ref, xs)[1],
-            "ks_p_vs_fp64_n1e4": stats.ks_2samp(ref[:10000], xs[:10000])[1], "w1_vs_fp64": stats.wasserstein1(ref, xs),
+            "speedup_vs_fp64": rate / fp64_rate, "ks_p_vs_fp64": float(sst.ks_2samp(ref, xs)[1]),
+            "ks_p_vs_fp64_n1e4": float(sst.ks_2samp(ref[:10000], xs[:10000])[1]),
+            "w1_vs_fp64": float(sst.wasserstein_distance(ref, xs)),
             "mean": float(xs.mean()), "var": float(xs.var()), "ops_per_event": ops_per_event(prec, rnd)}
     modes_out["fp64:rn"] = {"events_per_s": fp64_rate, "ms_per_launch": float(np.mean(fp64_ms)),
                             "mean": float(ref.mean()), "var": float(ref.var())}
@@ -457,6 +462,282 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+# ===================================================== tau-leaping and RDME
+# The same contract for the two approximate / spatial extensions of the path:
+#   --workload tau   fixed-leap tau-leaping on the Schloegl configuration above
+#                    (10^6 trajectories per GPU, t_end = 10, 50 snapshots,
+#                    tau = 0.005 = 2000 leaps); unit: reactions fired (the sum
+#                    of the Poisson counts) per second;
+#   --workload rdme  the spatial Schloegl chain: 32 voxels in a line, each the
+#                    Schloegl system above, X hopping at D = 1 per molecule to
+#                    each neighbour, 2^17 lattices per GPU, t_end = 2, one
+#                    snapshot; unit: events (reactions + hops) per second.
+# A step runs the listed modes one after the other, each timed with CUDA
+# events on the launching stream; fp64 is timed beside the step on a smaller
+# ensemble.  Roofline: the kernels are bound by instruction issue (state in
+# registers / shared memory, HBM carries only snapshots), so `achieved` is the
+# warp-instruction rate = (warp instructions per unit from one ncu count,
+# keyed by the device-source hash) x (units per second measured here) and
+# `peak` = SMs x 4 warp instructions per clock x the sampled SM clock.
+TAU_STEP = 0.005
+TAU_MODES = [("fp32", "rn"), ("mixed_f16", "rn"), ("mixed_bf16", "rn"), ("uniform_f16", "sr"), ("uniform_bf16", "sr")]
+TAU_N_TRAJ = 1_000_000
+TAU_FP64_TRAJ = 200_000
+RDME_S = 32
+RDME_D = [1.0, 0.0, 0.0]
+RDME_T_END = 2.0
+RDME_MODES = [("fp32", "rn"), ("mixed_f16", "rn"), ("mixed_bf16", "rn"), ("mixed_f16", "sr")]
+RDME_N = 131_072
+RDME_FP64_N = 8192
+RDME_CAP = 4_000_000
+
+# ncu counts per unit (warp instructions; DRAM bytes), keyed by (device-source
+# hash, workload, mode); a changed kernel reports null until re-counted.
+NCU_PER_UNIT = {}
+
+
+def ext_source_hash(workload):
+    import hashlib
+    h = hashlib.sha256()
+    files = ["ssa_device.cuh", "ssa_models.h", "ssa_launch.h"]
+    files += ["tau_device.cuh", "ssa_k_tau.cu"] if workload == "tau" else ["rdme_device.cuh", "ssa_k_rdme.cu",
+                                                                          "ssa_k_rdme_schlogl.cu"]
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2605_00479_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ext_spec(workload, n_traj=None):
+    m = P.schlogl()
+    x0 = P.schlogl_x0(m)
+    if workload == "tau":
+        n = n_traj or TAU_N_TRAJ
+        samples = P.even_samples(T_END, K_SAMPLES)
+        return {"metric": "tau-leaping reactions/s on 1 GB300 (Schloegl, tau = 0.005), 16-bit and fp32 modes vs fp64",
+                "unit": "reactions/s", "modes": TAU_MODES, "n": n, "n64": min(n, TAU_FP64_TRAJ), "model": m,
+                "x0": x0, "samples": samples, "flush_l2": False,
+                "config": {"workload": f"schlogl bistable tau-leaping, {n} trajectories per GPU, t_end={T_END}, "
+                                       f"tau={TAU_STEP} ({int(round(T_END / TAU_STEP))} leaps), {K_SAMPLES} "
+                                       "snapshots, reservoirs folded, int32 state",
+                           "model": "schlogl", "n_traj_per_gpu": n, "tau": TAU_STEP, "t_end": T_END,
+                           "n_samples": K_SAMPLES, "modes": [f"{p}:{r}" for p, r in TAU_MODES],
+                           "baseline_mode": "fp64", "l2": "no input reuse; each launch writes 600 MB of snapshots "
+                                                          "(> 129 MB L2)"}}
+    n = n_traj or RDME_N
+    lat = np.tile(x0, (RDME_S, 1)).astype(np.int32)
+    return {"metric": "RDME events/s on 1 GB300 (spatial Schloegl chain, 32 voxels), 16-bit and fp32 modes vs fp64",
+            "unit": "events/s", "modes": RDME_MODES, "n": n, "n64": min(n, RDME_FP64_N), "model": m, "x0": lat,
+            "samples": [RDME_T_END], "flush_l2": True,
+            "config": {"workload": f"RDME spatial schlogl chain, {RDME_S} voxels, D=1 for X, {n} lattices per GPU, "
+                                   f"t_end={RDME_T_END}, 1 snapshot, reservoirs folded, int32 state",
+                       "model": "schlogl", "lattice": [RDME_S, 1, 1], "diffusion": RDME_D, "n_traj_per_gpu": n,
+                       "t_end": RDME_T_END, "n_samples": 1, "modes": [f"{p}:{r}" for p, r in RDME_MODES],
+                       "baseline_mode": "fp64", "max_events": RDME_CAP,
+                       "l2": "lattice state lives in shared memory; a 256 MB buffer is written between launches "
+                             "(L2 flush)"}}
+
+
+def ext_launch(ssa, workload, spec, model, mode, n, seed, offset, stream, bufs=None):
+    prec, rnd = mode
+    kw = {} if bufs is None else dict(out=bufs[0], status=bufs[1], n_events=bufs[2], t_final=bufs[3])
+    if workload == "tau":
+        return ssa.tau_run(model, n, spec["x0"], T_END, TAU_STEP, spec["samples"], prec, rnd, True, seed, 4,
+                           stream=stream, traj_offset=offset, **kw)
+    return ssa.rdme_run(model, (RDME_S,), RDME_D, spec["x0"], n, RDME_T_END, spec["samples"], prec, rnd, True, seed,
+                        RDME_CAP, 4, stream=stream, traj_offset=offset, **kw)
+
+
+def ext_oracle_sample(workload, spec, modes, n_per_mode, workers):
+    """The oracle (as it stands) on a bounded sample: trajectory ids 0..n-1."""
+    import oracle
+    units = 0
+    t0 = time.perf_counter()
+    for prec, rnd in modes:
+        if workload == "tau":
+            r = oracle.events_parallel("tau_run", n_per_mode, workers=workers, model=spec["model"], x0=spec["x0"],
+                                       t_end=T_END, tau=TAU_STEP, sample_times=spec["samples"], precision=prec,
+                                       rounding=rnd, normalise=True, seed=SEED)
+        else:
+            r = oracle.events_parallel("rdme_run", n_per_mode, workers=workers, model=spec["model"],
+                                       dims=(RDME_S,), diffusion=RDME_D, x0=spec["x0"], t_end=RDME_T_END,
+                                       sample_times=spec["samples"], precision=prec, rounding=rnd, normalise=True,
+                                       seed=SEED, max_events=RDME_CAP)
+        units += int(r["n_events"].sum())
+    return units, time.perf_counter() - t0
+
+
+def ext_oracle_n(workload, workers):
+    return (64 if workload == "tau" else 16) * workers
+
+
+def run_ext_reference(args, world, rank, workload):
+    if rank != 0:
+        return
+    spec = ext_spec(workload)
+    workers = os.cpu_count() or 1
+    n = ext_oracle_n(workload, workers)
+    for _ in range(args.warmup):
+        ext_oracle_sample(workload, spec, spec["modes"], workers, workers)
+    times, units = [], []
+    for _ in range(args.steps):
+        u, dt = ext_oracle_sample(workload, spec, spec["modes"], n, workers)
+        times.append(dt)
+        units.append(u)
+    value = sum(units) / sum(times)
+    sample = f"{n} trajectories per mode per step (of {spec['n']}), ids 0..{n - 1}"
+    print(json.dumps({
+        "impl": "reference", "metric": spec["metric"], "value": value, "unit": spec["unit"], "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32,f16,bf16",
+        "data": "synthetic", "config": spec["config"],
+        "cpu_baseline": {"value": value, "unit": spec["unit"], "cores": workers, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": spec["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+        flush=True)
+
+
+def run_ext(args, world, rank, local, workload):
+    import torch
+    from scipy import stats as sst
+    from paper_2605_00479_gb300 import ssa
+
+    torch.cuda.set_device(local)
+    ssa.lib()
+    spec = ext_spec(workload, args.n_traj)
+    if args.modes:
+        spec["modes"] = [tuple(m.split(":")) for m in args.modes.split(",")]
+    model = ssa.Model.from_dict(spec["model"])
+    n, n64 = spec["n"], spec["n64"]
+    offset = rank * n
+    main = torch.cuda.current_stream()
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.int32, device="cuda") if spec["flush_l2"] else None
+
+    N = model.N
+    shape = (len(spec["samples"]), N, n) if workload == "tau" else (len(spec["samples"]), RDME_S, N, n)
+
+    def buffers(count):
+        sh = shape[:-1] + (count,)
+        return (torch.empty(sh, dtype=torch.int32, device="cuda"), torch.empty(count, dtype=torch.int32, device="cuda"),
+                torch.empty(count, dtype=torch.int64, device="cuda"),
+                torch.empty(count, dtype=torch.float64, device="cuda"))
+
+    bufs = {mode: buffers(n) for mode in spec["modes"]}
+    bufs[("fp64", "rn")] = buffers(n64)
+
+    def step(modes, seed, count):
+        per = []
+        for mode in modes:
+            if flush is not None:
+                flush.fill_(1)                  # between launches, outside the timed interval
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(main)
+            r = ext_launch(ssa, workload, spec, model, mode, count, seed, offset, main, bufs[mode])
+            e1.record(main)
+            per.append((mode, e0, e1, r))
+        torch.cuda.synchronize()
+        out = {}
+        for mode, e0, e1, r in per:
+            out[mode] = (e0.elapsed_time(e1), float(r["n_events"].double().sum()),
+                         r["snapshots"][-1, 0].cpu().numpy() if workload == "tau" else
+                         r["snapshots"][-1, RDME_S // 2, 0].cpu().numpy(),
+                         int(((r["status"].cpu().numpy() & 0x9) != 0).sum()))
+        return out
+
+    for _ in range(args.warmup):
+        step(spec["modes"], SEED, n)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = [step(spec["modes"], SEED, n) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    barrier(world)
+    clocks.stop()
+    local_time = sum(v[0] for st in steps for v in st.values()) / 1e3
+    local_units = sum(v[1] for st in steps for v in st.values())
+    job_time = max_over_ranks(world, local_time)
+    job_units = sum_over_ranks(world, local_units)
+
+    # fp64 beside the step (smaller ensemble), and its states for accuracy
+    step([("fp64", "rn")], SEED + 1, n64)
+    r64 = step([("fp64", "rn")], SEED + 1, n64)[("fp64", "rn")]
+    fp64_rate = r64[1] / (r64[0] / 1e3)
+
+    # end to end through the public call: inputs from the host, results read back
+    h2d = d2h = 0
+    e2e_units, e2e_time = 0.0, 0.0
+    pinned = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
+              for k, v in zip(("snapshots", "status", "n_events", "t_final"), bufs[spec["modes"][0]])}
+    for mode in spec["modes"]:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = ext_launch(ssa, workload, spec, model, mode, n, SEED, offset, main, bufs[mode])   # inputs from host
+        for k, v in r.items():
+            pinned[k].copy_(v, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_time += time.perf_counter() - t1
+        e2e_units += float(pinned["n_events"].double().sum())
+        h2d += np.asarray(spec["x0"]).size * 4 + 8 * len(spec["samples"])
+        d2h += sum(v.numel() * v.element_size() for v in pinned.values())
+    e2e_time = max_over_ranks(world, e2e_time)
+    e2e_units = sum_over_ranks(world, e2e_units)
+    if rank != 0:
+        return
+
+    ref = r64[2]
+    modes_out = {"fp64:rn": {"units_per_s": fp64_rate, "ms_per_launch": r64[0], "n_traj": n64,
+                             "mean": float(ref.mean()), "var": float(ref.var())}}
+    for mode in spec["modes"]:
+        ms = [st[mode][0] for st in steps]
+        u = sum(st[mode][1] for st in steps)
+        xs = steps[-1][mode][2]
+        modes_out[f"{mode[0]}:{mode[1]}"] = {
+            "units_per_s": u / (sum(ms) / 1e3), "ms_per_launch": float(np.mean(ms)),
+            "units_per_launch": steps[-1][mode][1],
+            "speedup_vs_fp64": (u / (sum(ms) / 1e3)) / fp64_rate,
+            "ks_p_vs_fp64": float(sst.ks_2samp(ref, xs)[1]), "w1_vs_fp64": float(sst.wasserstein_distance(ref, xs)),
+            "mean": float(xs.mean()), "var": float(xs.var()), "stopped": steps[-1][mode][3]}
+    dom = max(spec["modes"], key=lambda m: sum(st[m][0] for st in steps))
+    dom_ms = float(np.mean([st[dom][0] for st in steps]))
+    dom_units = float(np.mean([st[dom][1] for st in steps]))
+    clk = clocks.summary()
+    sm_mhz = clk["sm_mhz"] or 1455.0
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    key = (ext_source_hash(workload), workload, f"{dom[0]}:{dom[1]}")
+    counts = NCU_PER_UNIT.get(key)
+    peak = sms * 4 * sm_mhz * 1e6 / 1e9
+    achieved = None if counts is None else counts["warp_inst"] * dom_units / (dom_ms / 1e3) / 1e9
+    value = job_units / job_time
+    line = {
+        "metric": spec["metric"], "value": value, "unit": spec["unit"], "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * job_time / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32,f16,bf16", "data": "synthetic",
+        "config": spec["config"], "gpu_launches": len(spec["modes"]) * args.steps,
+        "roofline": {"bound": "issue", "kernel": f"{workload}_kernel<schlogl,{dom[0]},{dom[1]}>",
+                     "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
+                     "frac": None if achieved is None else achieved / peak,
+                     "traffic": None if counts is None else counts["dram_bytes"] * dom_units,
+                     "traffic_unit": "bytes per launch", "source_hash": key[0],
+                     "peak_basis": f"{sms} SMs x 4 warp instructions per clock x {sm_mhz:.0f} MHz (median SM clock "
+                                   "sampled in the run)",
+                     "count_basis": "ncu smsp__inst_executed.sum per unit of the same kernel and source, times the "
+                                    "units per second measured here"},
+        "fp64_units_per_s": fp64_rate, "speedup_vs_fp64": value / fp64_rate, "modes": modes_out,
+        "e2e": {"value": e2e_units / e2e_time, "unit": spec["unit"], "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "clocks": clk, "wall_s_timed": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        workers = os.cpu_count() or 1
+        nn = ext_oracle_n(workload, workers)
+        u, dt = ext_oracle_sample(workload, spec, spec["modes"], nn, workers)
+        line["cpu_baseline"] = {"value": u / dt, "unit": spec["unit"], "cores": workers, "kind": "oracle",
+                                "sample": f"{nn} trajectories per mode (ids 0..{nn - 1}) of the same workload, "
+                                          "one process per core"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -469,6 +750,8 @@ def main():
     ap.add_argument("--n-traj", type=int, default=None,
                     help="trajectories per GPU (default 10^6; smaller values are for profiling only)")
     ap.add_argument("--modes", default=None, help="comma list like mixed_f16:rn (profiling only)")
+    ap.add_argument("--workload", choices=["schlogl", "tau", "rdme"], default="schlogl",
+                    help="schlogl: the direct-method benchmark (default); tau: tau-leaping; rdme: spatial RDME")
     args = ap.parse_args()
     global N_TRAJ, MODES16
     if args.n_traj:
@@ -476,7 +759,12 @@ def main():
     if args.modes:
         MODES16 = [tuple(m.split(":")) for m in args.modes.split(",")]
     world, rank, local = dist_setup(args)
-    if args.impl == "reference":
+    if args.workload != "schlogl":
+        if args.impl == "reference":
+            run_ext_reference(args, world, rank, args.workload)
+        else:
+            run_ext(args, world, rank, local, args.workload)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)

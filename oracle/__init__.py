@@ -288,3 +288,27 @@ def rdme_run(model, dims, diffusion, x0, n_traj, t_end, sample_times, precision=
     if rc != 0:
         raise ValueError("oracle_rdme_run rejected its arguments")
     return {"snapshots": out, "status": status, "n_events": nev, "t_final": tf}
+
+
+def _named_chunk(job):
+    fn = {"tau_run": tau_run, "rdme_run": rdme_run}[job.pop("fn")]
+    r = fn(**job)
+    return {"n_events": r["n_events"], "status": r["status"]}
+
+
+def events_parallel(fn, n_traj, workers=None, **kw):
+    """Event counts and status of ``tau_run`` or ``rdme_run`` (named by ``fn``)
+    over trajectory ids g0 .. g0+n_traj-1, split over a spawned process pool
+    (trajectories are independent, so this only shortens wall time)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    workers = workers or max(1, min(os.cpu_count() or 1, 16))
+    g0 = int(kw.pop("g0", 0))
+    bounds = np.linspace(0, n_traj, workers + 1).astype(np.int64)
+    jobs = [dict(fn=fn, n_traj=int(b - a), g0=g0 + int(a), **kw) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+    if len(jobs) == 1:
+        return _named_chunk(jobs[0])
+    with cf.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_named_chunk, jobs))
+    return {"n_events": np.concatenate([p["n_events"] for p in parts]),
+            "status": np.concatenate([p["status"] for p in parts])}

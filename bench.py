@@ -91,8 +91,8 @@ def ops_per_event(prec, rnd):
 # trajectories).  Valid only for the kernel source it was measured on: the
 # key includes a hash of the device code, and a changed kernel reports null.
 NCU_TRAFFIC_PER_TRAJ = {
-    # uniform_f16 RN, 3e5 trajectories: 272,201,216 B read + 446,491,136 B written
-    ("95b12a1602e75ec8", "uniform_f16:rn"): (272201216 + 446491136) / 300000,
+    # uniform_f16 RN, 3e5 trajectories: 274,445,824 B read + 447,058,944 B written
+    ("2f0c5b3a6f0732d0", "uniform_f16:rn"): (274445824 + 447058944) / 300000,
 }
 
 

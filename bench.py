@@ -494,13 +494,13 @@ RDME_CAP = 4_000_000
 # ncu counts per unit (warp instructions; DRAM bytes), keyed by (device-source
 # hash, workload, mode); a changed kernel reports null until re-counted.
 NCU_PER_UNIT = {
-    # tau, 2e5 trajectories, one launch per mode (profiles/tau_leaping_bench_schlogl.md)
+    # tau, 2e5 trajectories, one launch per mode
     ("82380294efe007d5", "tau", "fp32:rn"): {"warp_inst": 6.795, "dram_bytes": 0.02867},
     ("82380294efe007d5", "tau", "mixed_f16:rn"): {"warp_inst": 6.928, "dram_bytes": 0.01969},
     ("82380294efe007d5", "tau", "mixed_bf16:rn"): {"warp_inst": 6.791, "dram_bytes": 0.01947},
     ("82380294efe007d5", "tau", "uniform_f16:sr"): {"warp_inst": 7.527, "dram_bytes": 0.02130},
     ("82380294efe007d5", "tau", "uniform_bf16:sr"): {"warp_inst": 7.396, "dram_bytes": 0.02072},
-    # rdme, 32768 lattices, one launch per mode (profiles/rdme_schlogl_chain.md)
+    # rdme, 32768 lattices, one launch per mode
     ("c0755ae3d51c58b6", "rdme", "fp32:rn"): {"warp_inst": 27.384, "dram_bytes": 0.00012},
     ("c0755ae3d51c58b6", "rdme", "mixed_f16:rn"): {"warp_inst": 29.566, "dram_bytes": 0.00017},
     ("c0755ae3d51c58b6", "rdme", "mixed_bf16:rn"): {"warp_inst": 29.552, "dram_bytes": 0.00063},

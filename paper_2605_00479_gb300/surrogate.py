@@ -9,7 +9,7 @@ Workflow (host orchestration of the CUDA kernels in libssa_gb300.so):
   2. Training: the 4 -> 256 -> 256 -> 256 -> 128 GELU network on the tensor
      cores (tcgen05 GEMMs, bf16 operands, fp32 accumulation), AdamW with a
      cosine learning-rate schedule, cross-entropy against the histograms.
-  3. Serving: predictions for query points; the SSA is the judge: each query
+  3. Serving: predictions for query points, checked against the SSA: each query
      point's prediction is compared with a fresh SSA ensemble (Wasserstein-1
      in copies) and points above the threshold (0.5 copies) are answered by
      re-simulation instead.
@@ -83,16 +83,16 @@ def train(net, feats, hists, steps, batch_size, lr_max=2e-3, lr_min=5e-5, weight
     return trace
 
 
-def serve(net, query_params, judge_hist):
-    """Predict, judge against an SSA ensemble, fall back where W1 > threshold.
+def serve(net, query_params, ref_hist):
+    """Predict, compare with an SSA ensemble, fall back where W1 > threshold.
 
     Returns (answer histograms, per-point W1 of the prediction, fallback mask)."""
     import torch
     feats = torch.from_numpy(standardise(query_params)).cuda()
     q = net.predict(feats)
-    w1 = ssa.hist_w1(q, judge_hist)
+    w1 = ssa.hist_w1(q, ref_hist)
     fallback = w1 > W1_THRESHOLD
-    answer = torch.where(fallback[:, None], judge_hist, q)
+    answer = torch.where(fallback[:, None], ref_hist, q)
     return answer, w1, fallback
 
 
@@ -123,7 +123,7 @@ def run(n_train=2**16, traj_train=1024, n_query=2**14, traj_query=1024, steps=60
     # 3. serving on held-out points against fresh SSA ensembles
     qp = draw_parameters(n_query, seed + 1)
     t0 = time.perf_counter()
-    judge = simulate_histograms(qp, traj_query, seed=seed + 7, traj_offset=2**31)
+    ref = simulate_histograms(qp, traj_query, seed=seed + 7, traj_offset=2**31)
     torch.cuda.synchronize()
     ssa_s = time.perf_counter() - t0
     twin = simulate_histograms(qp, traj_query, seed=seed + 8, traj_offset=2**31)   # SSA-vs-SSA noise floor
@@ -137,8 +137,8 @@ def run(n_train=2**16, traj_train=1024, n_query=2**14, traj_query=1024, steps=60
         net.predict(feats_q)
     torch.cuda.synchronize()
     nn_s = (time.perf_counter() - t0) / reps
-    answer, w1, fallback = serve(net, qp, judge)
-    noise = ssa.hist_w1(twin, judge)
+    answer, w1, fallback = serve(net, qp, ref)
+    noise = ssa.hist_w1(twin, ref)
     w1_ans = ssa.hist_w1(answer, twin)
     torch.cuda.synchronize()
     w1n, noisen = w1.cpu().numpy(), noise.cpu().numpy()

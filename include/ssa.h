@@ -154,7 +154,10 @@ int ssa_ensemble_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offse
  * call allocates device buffers, launches, copies the results back and
  * synchronises the stream before returning.  out, traj_status, n_events and
  * t_final are host pointers with the layouts above (n_events, t_final may be
- * NULL).  Page-locked host memory makes the copies faster.
+ * NULL).  Page-locked host memory makes the copies faster.  The device
+ * buffers come from a memory pool private to the library that keeps its
+ * reservation between calls (the largest call's size, per device, until the
+ * process exits), so repeated calls do not remap device memory.
  */
 int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_offset,
                           const int32_t *x0, double t_end, int n_samples, const double *sample_times,

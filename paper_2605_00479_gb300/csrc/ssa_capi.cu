@@ -189,6 +189,60 @@ void fill_structure(const ssa_model &m, int normalise, const int32_t *x0, ssa::R
     for (int i = 0; i < m.N; ++i) a.x0[i] = x0[i];
 }
 
+// One launch over trajectories traj_offset .. traj_offset + n_work - 1 whose
+// outputs sit in columns 0 .. n_work - 1 of arrays with `stride` columns
+// (out, status, n_events and t_final already point at the first column).
+// Arguments are validated by the caller.
+int launch_run(const ssa_model *model, int64_t n_work, int64_t stride, uint64_t traj_offset, const int32_t *x0,
+               double t_end, int n_samples, const double *sample_times, int precision, int rounding, int normalise,
+               uint64_t seed, int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
+               int64_t *n_events, double *t_final, cudaStream_t s)
+{
+    ssa::RunArgs *a = new (std::nothrow) ssa::RunArgs;
+    if (!a) return fail(SSA_ENOMEM, "out of host memory");
+    std::memset(a, 0, sizeof(*a));
+    fill_structure(*model, normalise, x0, *a);
+    a->K = n_samples;
+    a->n_traj = stride;
+    a->n_work = n_work;
+    a->slice_pairs = g_cfg.slice_pairs;
+    a->traj_offset = (uint32_t)traj_offset;
+    a->n_sets = 1;
+    a->traj_per_set = n_work;
+    a->t_end = t_end;
+    for (int k = 0; k < n_samples; ++k) a->samples[k] = sample_times[k];
+    a->key0 = (uint32_t)seed;
+    a->key1 = (uint32_t)(seed >> 32);
+    a->max_events = max_events;
+    a->out = out;
+    a->state_bytes = state_bytes;
+    a->status = traj_status;
+    a->n_events = n_events;
+    a->t_final = t_final;
+
+    unsigned long long *head = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&head), sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        delete a;
+        return e == cudaErrorMemoryAllocation ? fail(SSA_ENOMEM, "work-queue counter: out of device memory")
+                                              : cuda_fail(e, "cudaMallocAsync");
+    }
+    e = cudaMemsetAsync(head, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(head, s);
+        delete a;
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    a->queue_head = head;
+    int grid = 0;
+    e = launcher_for(model->family)(*a, precision, rounding, normalise ? 1 : 0, g_cfg, s, &grid);
+    cudaError_t e2 = cudaFreeAsync(head, s);
+    delete a;
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return SSA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -277,53 +331,57 @@ int ssa_ensemble_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offse
     if (rc != SSA_OK) return rc;
     if (n_traj > 0 && (!out || !traj_status)) return fail(SSA_EINVAL, "out and traj_status are required");
     if (n_traj == 0) return SSA_OK;
-
-    ssa::RunArgs *a = new (std::nothrow) ssa::RunArgs;
-    if (!a) return fail(SSA_ENOMEM, "out of host memory");
-    std::memset(a, 0, sizeof(*a));
-    fill_structure(*model, normalise, x0, *a);
-    a->K = n_samples;
-    a->n_traj = n_traj;
-    a->n_work = n_traj;
-    a->slice_pairs = g_cfg.slice_pairs;
-    a->traj_offset = (uint32_t)traj_offset;
-    a->n_sets = 1;
-    a->traj_per_set = n_traj;
-    a->t_end = t_end;
-    for (int k = 0; k < n_samples; ++k) a->samples[k] = sample_times[k];
-    a->key0 = (uint32_t)seed;
-    a->key1 = (uint32_t)(seed >> 32);
-    a->max_events = max_events;
-    a->out = out;
-    a->state_bytes = state_bytes;
-    a->status = traj_status;
-    a->n_events = n_events;
-    a->t_final = t_final;
-
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    unsigned long long *head = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&head), sizeof(unsigned long long), s);
-    if (e != cudaSuccess) {
-        delete a;
-        return e == cudaErrorMemoryAllocation ? fail(SSA_ENOMEM, "work-queue counter: out of device memory")
-                                              : cuda_fail(e, "cudaMallocAsync");
-    }
-    e = cudaMemsetAsync(head, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(head, s);
-        delete a;
-        return cuda_fail(e, "cudaMemsetAsync");
-    }
-    a->queue_head = head;
-    const bool norm = normalise != 0;
-    int grid = 0;
-    e = launcher_for(model->family)(*a, precision, rounding, norm ? 1 : 0, g_cfg, s, &grid);
-    cudaError_t e2 = cudaFreeAsync(head, s);
-    delete a;
-    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
-    return SSA_OK;
+    return launch_run(model, n_traj, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
+                      normalise, seed, max_events, state_bytes, out, traj_status, n_events, t_final,
+                      static_cast<cudaStream_t>(stream));
 }
+
+}  // extern "C"
+
+namespace {
+
+// Staging memory of the host-buffer entry point comes from a stream-ordered
+// pool private to this library whose reservation survives between calls
+// (release threshold at the maximum): repeated calls reuse the same device
+// pages instead of mapping and unmapping hundreds of megabytes each time.
+// The reservation is returned when the process exits.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_staging_pool[kMaxPoolDevices];
+bool g_staging_ready[kMaxPoolDevices];
+
+cudaError_t staging_pool(cudaMemPool_t *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_staging_ready[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_staging_pool[dev] = pool;
+        g_staging_ready[dev] = true;
+    }
+    *out = g_staging_pool[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
 
 int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, const int32_t *x0,
                           double t_end, int n_samples, const double *sample_times, int precision, int rounding,
@@ -342,16 +400,19 @@ int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_
     const size_t tf_bytes = t_final ? (size_t)n_traj * sizeof(double) : 0;
     char *d = nullptr;
     const size_t total = out_bytes + st_bytes + ev_bytes + tf_bytes + 64;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d), total, s);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(SSA_ENOMEM, "device buffers") : cuda_fail(e, "cudaMallocAsync");
+    cudaMemPool_t pool;
+    cudaError_t e = staging_pool(&pool);
+    if (e != cudaSuccess) return cuda_fail(e, "staging memory pool");
+    e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&d), total, pool, s);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(SSA_ENOMEM, "device buffers") : cuda_fail(e, "cudaMallocFromPoolAsync");
     // 8-byte aligned sub-buffers: int64/double arrays first
     char *p = d;
     int64_t *d_ev = ev_bytes ? reinterpret_cast<int64_t *>(p) : nullptr; p += ev_bytes;
     double *d_tf = tf_bytes ? reinterpret_cast<double *>(p) : nullptr; p += tf_bytes;
     uint32_t *d_st = reinterpret_cast<uint32_t *>(p); p += st_bytes;
     void *d_out = p;
-    rc = ssa_ensemble_run(model, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
-                          normalise, seed, max_events, state_bytes, d_out, d_st, d_ev, d_tf, stream);
+    rc = launch_run(model, n_traj, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
+                    normalise, seed, max_events, state_bytes, d_out, d_st, d_ev, d_tf, s);
     if (rc == SSA_OK) {
         e = cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(traj_status, d_st, st_bytes, cudaMemcpyDeviceToHost, s);

@@ -162,6 +162,21 @@ def test_host_entry_point_matches_device(ssa):
     assert_same({**h, "status": h["status"].view(np.int32)}, {**g, "status": g["status"].view(np.uint32)})
 
 
+@pytest.mark.parametrize("state_bytes", [4, 2])
+def test_large_host_entry_point_matches_device(ssa, state_bytes):
+    """The host entry point (staging memory from the library's pool) at 3e5
+    trajectories with an id offset equals the device entry point."""
+    tel = P.telegraph(0.5, 0.5, 20.0, 1.0)
+    m = ssa.Model.from_dict(tel)
+    n, off = 300001, 12345
+    samples = P.even_samples(5.0, 4)
+    h = ssa.ensemble_run_host(m, n, P.TELEGRAPH_X0, 5.0, samples, "uniform_bf16", "sr", seed=31, max_events=10**5,
+                              state_bytes=state_bytes, traj_offset=off)
+    g, _ = gpu_run(ssa, tel, P.TELEGRAPH_X0, n, 5.0, samples, "uniform_bf16", "sr", False, 31, 10**5,
+                   state_bytes=state_bytes, traj_offset=off)
+    assert_same({**h, "status": h["status"].view(np.int32)}, {**g, "status": g["status"].view(np.uint32)})
+
+
 BENCH_MODES = [("mixed_f16", "rn"), ("mixed_bf16", "rn"), ("uniform_f16", "rn"), ("uniform_f16", "sr"),
                ("uniform_bf16", "sr"), ("uniform_f16", "sra"), ("mixed_f16", "sr")]
 

@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x;
-    const uint32_t ncols = g.N <= 32 ? 32u : (g.N <= 64 ? 64u : (g.N <= 128 ? 128u : 256u));
+    const int nt = g.ntile, n0 = blockIdx.y * nt;     // this CTA's columns n0 .. n0 + nt - 1
+    const uint32_t ncols = nt <= 32 ? 32u : (nt <= 64 ? 64u : (nt <= 128 ? 128u : 256u));
     if (warp == 0) tmem_alloc(&tmem_base_s, ncols);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -164,9 +165,9 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
     const uint32_t tmem_d = tmem_base_s;
 
     const int n_chunks = g.K / g.kchunk;
-    const uint32_t idesc = instr_desc_bf16_f32(kTileM, g.N);
+    const uint32_t idesc = instr_desc_bf16_f32(kTileM, nt);
     const uint32_t rg_bytes = (uint32_t)g.kchunk * 16u;   // one 8-row group of one stage
-    const uint32_t stage_bytes = (uint32_t)(kTileM + g.N) * (uint32_t)g.kchunk * 2u;
+    const uint32_t stage_bytes = (uint32_t)(kTileM + nt) * (uint32_t)g.kchunk * 2u;
     int err = ERR_NONE;
     int ch = 0;
     for (; ch < n_chunks; ++ch) {
@@ -175,14 +176,15 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
             if (lane == 0) mbar_expect_tx(&bars[0], stage_bytes);
             __syncwarp();
             const int colA = g.a_col0 + ch * g.kchunk, colB = g.b_col0 + ch * g.kchunk;
-            const int groups = kTileM / 8 + g.N / 8;
+            const int groups = kTileM / 8 + nt / 8;
             for (int q = lane; q < groups; q += 32) {
                 if (q < kTileM / 8) {
                     const int64_t rg = (int64_t)tile * (kTileM / 8) + q;
                     bulk_g2s(sA + (size_t)q * rg_bytes, g.A + (rg * (g.lda_cols / 8) + colA / 8) * 128, rg_bytes, &bars[0]);
                 } else {
                     const int64_t rg = q - kTileM / 8;
-                    bulk_g2s(sB + (size_t)rg * rg_bytes, g.B + (rg * (g.ldb_cols / 8) + colB / 8) * 128, rg_bytes,
+                    const int64_t brg = (int64_t)(n0 / 8) + rg;
+                    bulk_g2s(sB + (size_t)rg * rg_bytes, g.B + (brg * (g.ldb_cols / 8) + colB / 8) * 128, rg_bytes,
                              &bars[0]);
                 }
             }
@@ -213,9 +215,10 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
     if (ok) {
         const int64_t row = (int64_t)tile * kTileM + warp * 32 + lane;
         const bool valid = row < g.m_valid;
-        for (int c0 = 0; c0 < g.N; c0 += 16) {
+        for (int cl = 0; cl < nt; cl += 16) {
+            const int c0 = n0 + cl;       // column of D
             float v[16];
-            tmem_ld16(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tmem_ld16(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)cl, v);
             if (g.epi == EPI_STORE_F32 || g.epi == EPI_LOGITS) {
                 if (valid) {
 #pragma unroll
@@ -291,16 +294,19 @@ cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s)
 {
     // Shared memory also caps how many CTAs share an SM: request enough that
     // their tensor-memory columns (ncols each) never exceed the SM's 512.
-    const int ncols = g.N <= 32 ? 32 : (g.N <= 64 ? 64 : (g.N <= 128 ? 128 : 256));
+    GemmArgs a = g;
+    a.ntile = (g.N >= 128 && g.N % 64 == 0) ? 64 : g.N;   // column tiles per row tile: N / ntile
+    const int ncols = a.ntile <= 32 ? 32 : (a.ntile <= 64 ? 64 : (a.ntile <= 128 ? 128 : 256));
     const size_t per_sm = 233472, reserve = 1024;
     const size_t cap_ctas = (size_t)(512 / ncols);
-    size_t smem = (size_t)(kTileM + g.N) * (size_t)g.kchunk * 2 + 128;
+    size_t smem = (size_t)(kTileM + a.ntile) * (size_t)g.kchunk * 2 + 128;
     const size_t floor_bytes = per_sm / (cap_ctas + 1) + 1 - reserve;
     if (smem < floor_bytes) smem = floor_bytes;
     cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int tiles = (g.M + kTileM - 1) / kTileM;
-    gemm_kernel<<<tiles, 128, smem, s>>>(g);
+    const dim3 grid((unsigned)tiles, (unsigned)(g.N / a.ntile));
+    gemm_kernel<<<grid, 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 

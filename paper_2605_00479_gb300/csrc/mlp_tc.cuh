@@ -1,8 +1,10 @@
 // mlp_tc.cuh -- tcgen05 (5th-generation tensor core) GEMM for the surrogate MLP.
 //
 // D[M x N] (fp32, in tensor memory) = sum over K of A[M x K] * B[N x K]^T with
-// A and B in bf16.  One CTA of 128 threads owns a 128-row tile of D and all
-// N <= 256 columns; the accumulator occupies N columns of tensor memory.
+// A and B in bf16.  One CTA of 128 threads owns a 128-row x ntile-column tile
+// of D (ntile = 64 when N >= 128 is a multiple of 64, else N; grid = row
+// tiles x column tiles); the accumulator occupies ntile columns of tensor
+// memory.
 //
 // Operands live in global memory in the "packed" layout that tcgen05 reads
 // without swizzling (K-major core matrices of 8 rows x 16 bytes):
@@ -43,6 +45,7 @@ struct GemmArgs {
     int lda_cols, ldb_cols;    // C of the packed A / B matrices
     int a_col0, b_col0;        // first reduction column used (multiple of 16)
     int M, N, K, kchunk;       // rows of D computed (tiles of 128), columns, reduction length, columns per stage
+    int ntile;                 // columns of D per CTA (set by launch_gemm)
     int m_valid;               // rows < m_valid are real; the others are written as zeros (or skipped)
     int epi;
     const float *bias;         // [N]

@@ -18,7 +18,7 @@ def ssa():
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 16, 16), (300, 256, 256), (257, 128, 512), (1024, 256, 16), (64, 64, 32),
-                                   (384, 16, 768)])
+                                   (384, 16, 768), (200, 192, 64), (130, 144, 48)])
 def test_gemm_matches_fp32_reference(ssa, M, N, K):
     """D = A B^T with bf16 operands and fp32 accumulation; the reference sums
     the same bf16 products in fp32 (differences come only from summation

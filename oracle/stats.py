@@ -67,3 +67,63 @@ def wasserstein1(a, b):
 def summary(sample):
     s = np.asarray(sample, dtype=np.float64)
     return {"mean": float(s.mean()), "var": float(s.var())}
+
+
+# --------------------------------------------------------------------------
+# Histogram-based statistics of integer ensembles (the device statistics
+# kernels follow the same definitions, so results compare exactly):
+#   count_histogram  h[k] = #{v = k} for k in 0..bins-1, values below 0 or
+#                    above bins-1 counted in the end bins and reported;
+#   hist_ks_w1       with C_a(k), C_b(k) the cumulative counts and n_a, n_b
+#                    the totals, diff(k) = |C_a(k) n_b - C_b(k) n_a| (exact
+#                    integers), D = max diff / (n_a n_b) and
+#                    W1 = (sum over k of diff) / (n_a n_b), each quotient
+#                    one IEEE division of the two integers rounded to
+#                    binary64 (NaN when a sample is empty or
+#                    bins n_a n_b >= 2^63);
+#   dwell_histogram  for each trajectory of a 0/1 series s[k] (k = 0..K-1,
+#                    nonzero = OFF), every completed OFF interval: the first
+#                    OFF sample after an ON sample starts it, the first ON
+#                    sample after that ends it; h[end - start] += 1.
+# --------------------------------------------------------------------------
+def count_histogram(values, bins):
+    v = np.asarray(values, dtype=np.int64).ravel()
+    clamped = int(np.count_nonzero((v < 0) | (v >= bins)))
+    return np.bincount(np.clip(v, 0, bins - 1), minlength=bins).astype(np.int64), clamped
+
+
+def hist_ks_w1(ha, hb):
+    ha = [int(x) for x in np.asarray(ha).ravel()]
+    hb = [int(x) for x in np.asarray(hb).ravel()]
+    na, nb = sum(ha), sum(hb)
+    if na == 0 or nb == 0 or len(ha) * na * nb >= 2**63:
+        return float("nan"), float("nan")
+    ca = cb = 0
+    dmax = 0
+    total = 0
+    for x, y in zip(ha, hb):
+        ca += x
+        cb += y
+        d = abs(ca * nb - cb * na)
+        dmax = max(dmax, d)
+        total += d
+    return float(dmax) / float(na * nb), float(total) / float(na * nb)
+
+
+def dwell_histogram(series):
+    """series [K, n]: nonzero = OFF; returns h [K] (h[d] = completed OFF intervals of d samples)."""
+    s = np.asarray(series)
+    K, n = s.shape
+    h = np.zeros(K, dtype=np.int64)
+    for j in range(n):
+        start = -1
+        prev_off = bool(s[0, j] != 0)
+        for k in range(1, K):
+            off = bool(s[k, j] != 0)
+            if off and not prev_off:
+                start = k
+            elif not off and prev_off and start >= 0:
+                h[k - start] += 1
+                start = -1
+            prev_off = off
+    return h

@@ -214,3 +214,41 @@ def test_ks_and_wasserstein_match_scipy():
         ne = 5000 * 3000 / 8000
         assert abs(p - scipy_stats.kstwobign.sf(D * np.sqrt(ne))) < 1e-9
         assert abs(stats.wasserstein1(a, b) - scipy_stats.wasserstein_distance(a, b)) < 1e-9
+
+
+def test_histogram_statistics_against_scipy_and_brute_force():
+    """The histogram form of KS and W1 equals scipy's sample-based values on
+    integer data; the dwell extraction equals an interval search written
+    differently (runs of equal values)."""
+    import scipy.stats as scipy_stats
+    from oracle import stats as ost
+    rng = np.random.default_rng(5)
+    for na, nb, lam1, lam2 in [(500, 700, 20.0, 21.5), (3000, 2000, 3.0, 3.0), (50, 4000, 100.0, 80.0)]:
+        a = rng.poisson(lam1, na)
+        b = rng.poisson(lam2, nb)
+        bins = int(max(a.max(), b.max())) + 3
+        ha, ca = ost.count_histogram(a, bins)
+        hb, cb = ost.count_histogram(b, bins)
+        assert ca == cb == 0 and ha.sum() == na and hb.sum() == nb
+        D, W1 = ost.hist_ks_w1(ha, hb)
+        assert abs(D - scipy_stats.ks_2samp(a, b).statistic) < 1e-12
+        assert abs(W1 - scipy_stats.wasserstein_distance(a, b)) < 1e-12
+    h, c = ost.count_histogram([-3, 0, 5, 9, 12], 10)
+    assert c == 2 and h[0] == 2 and h[9] == 2 and h[5] == 1
+    assert np.isnan(ost.hist_ks_w1(np.zeros(4), np.ones(4))[0])
+    # dwell: runs of OFF (nonzero) bounded by ON samples on both sides
+    s = rng.integers(0, 2, size=(60, 40))
+    want = np.zeros(60, dtype=np.int64)
+    for j in range(40):
+        col = s[:, j] != 0
+        runs, k = [], 0
+        while k < 60:
+            e = k
+            while e + 1 < 60 and col[e + 1] == col[k]:
+                e += 1
+            runs.append((col[k], k, e))
+            k = e + 1
+        for idx, (off, k0, k1) in enumerate(runs):
+            if off and idx > 0 and idx + 1 < len(runs):
+                want[k1 - k0 + 1] += 1
+    np.testing.assert_array_equal(ost.dwell_histogram(s), want)

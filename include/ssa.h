@@ -421,6 +421,40 @@ int ssa_histogram(const int32_t *counts, int64_t n_sets, int64_t traj_per_set, i
  * (device [rows][bins]): the Wasserstein-1 distance on the integers. */
 int ssa_hist_w1(const float *p, const float *q, int64_t rows, int bins, float *w1, void *stream);
 
+/*
+ * On-device ensemble statistics (the comparisons of Sec. 4: two-sample
+ * Kolmogorov-Smirnov statistic and Wasserstein-1 distance between the
+ * ensembles of two precision modes; dwell times of the telegraph gene,
+ * Sec. 4.3).  Integer-exact definitions:
+ *
+ * ssa_count_histogram -- hist[k] += #{values == k}, k = 0..bins-1 (device
+ *   uint64 [bins], ACCUMULATED: zero it first); values below 0 or above
+ *   bins-1 are counted in the end bins and added to *n_clamped (device).
+ *   values: device int32 (elem_bytes 4) or int16 (2), n of them; 1 <= bins
+ *   <= 2^24.  Asynchronous on stream.
+ *
+ * ssa_hist_ks_w1 -- out (device double [2]) = {D, W1} of the two samples
+ *   whose histograms are ha, hb (device uint64 [bins]): with cumulative
+ *   counts C_a, C_b and totals n_a, n_b, diff(k) = |C_a(k) n_b - C_b(k) n_a|
+ *   (64-bit integers), D = max diff / (n_a n_b), W1 = sum diff / (n_a n_b),
+ *   each the binary64 quotient of the two integers rounded to binary64.
+ *   NaN when a sample is empty or bins * n_a * n_b >= 2^63.  Asynchronous.
+ *
+ * ssa_dwell_histogram -- hist[d] += the number of completed OFF intervals of
+ *   d samples (device uint64 [K], ACCUMULATED) in the series
+ *   s[k * k_stride + j] (k = 0..K-1, trajectory j = 0..n-1, k_stride >= n;
+ *   device int32 or int16; nonzero = OFF): an interval starts at the first
+ *   OFF sample after an ON sample and ends at the first ON sample after it.
+ *   For snapshots [K][N][n] of species i: pass the address of element
+ *   (0, i, 0) and k_stride = N * n.  Asynchronous.
+ * Errors: SSA_EINVAL (arguments), SSA_ECUDA (launch).
+ */
+int ssa_count_histogram(const void *values, int elem_bytes, int64_t n, int bins, uint64_t *hist,
+                        uint64_t *n_clamped, void *stream);
+int ssa_hist_ks_w1(const uint64_t *ha, const uint64_t *hb, int bins, double *out, void *stream);
+int ssa_dwell_histogram(const void *series, int elem_bytes, int K, int64_t n, int64_t k_stride, uint64_t *hist,
+                        void *stream);
+
 /* Tensor-core GEMM check: D (device [M][N] fp32) = A (device [M][K] bf16,
  * row-major) times B (device [N][K] bf16, row-major) transposed.
  * N in 16..256 and a multiple of 16; K a multiple of 16 (of 256 above 256).

@@ -32,9 +32,12 @@ sweeps: the telegraph kon sweep (kon in [1e-3, 1e-1], koff = 0.1, alpha = 5,
 dwell: OFF-state dwell times of the bimodal telegraph set (kon = koff = 0.05,
   alpha = 20, beta = 1): the gene state is sampled at 1024 times to t_end = 200
   (spacing 0.196, 1% of the mean dwell 20); completed OFF intervals between
-  observed switches are compared with the exponential law of rate kon (mean
-  and KS distance of the sample against the exponential CDF evaluated at the
-  observed, grid-rounded durations) and across precision modes.
+  observed switches (extracted on the device) are compared with the
+  exponential law of rate kon (mean and KS distance of the sample against the
+  exponential CDF evaluated at the observed, grid-rounded durations) and
+  across precision modes (device KS / W1).
+Two-sample KS statistics and W1 distances in every command are computed on the
+device from histograms (ssa_count_histogram, ssa_hist_ks_w1).
 tau: fixed-leap tau-leaping in reduced precision (the combination the paper
   leaves open): Schloegl (bistable set, normalised, X0 = 250, t_end = 10) and
   dimerisation (M0 = 300, t_end = 20), leaps tau in {0.02, 0.005, 0.001} and
@@ -163,10 +166,23 @@ def _final_states(model_dict, x0, n, t_end, prec, rnd, normalise, seed, species,
 
 
 def _compare(ref, x):
+    """KS p-value, W1, mean and variance of sample x against ref (integer
+    counts).  D and W1 come from the device statistics kernels
+    (ssa_count_histogram, ssa_hist_ks_w1); p is the asymptotic Kolmogorov
+    tail of D sqrt(n_a n_b / (n_a + n_b))."""
+    import torch
     from scipy import stats as sst
-    w1 = float(sst.wasserstein_distance(ref, x))
-    p = float(sst.ks_2samp(ref, x).pvalue)
-    return {"ks_p": p, "w1": w1, "mean": float(x.mean()), "var": float(x.var())}
+    a = torch.as_tensor(np.ascontiguousarray(ref, dtype=np.int32)).cuda()
+    b = torch.as_tensor(np.ascontiguousarray(x, dtype=np.int32)).cuda()
+    lo = int(min(a.min().item(), b.min().item()))
+    bins = int(max(a.max().item(), b.max().item())) - lo + 1
+    ha, _ = ssa.count_histogram((a - lo).contiguous(), bins)
+    hb, _ = ssa.count_histogram((b - lo).contiguous(), bins)
+    D, w1 = (float(v) for v in ssa.hist_ks_w1(ha, hb).cpu().numpy())
+    ne = a.numel() * b.numel() / (a.numel() + b.numel())
+    p = float(sst.kstwobign.sf(D * np.sqrt(ne)))
+    xs = np.asarray(x, dtype=np.float64)
+    return {"ks_p": p, "ks_d": D, "w1": w1, "mean": float(xs.mean()), "var": float(xs.var())}
 
 
 def tables(scale=1, seed=11):
@@ -218,24 +234,26 @@ def sweeps(seed=21):
     return out
 
 
-def _off_dwells(goff, dt):
-    """Durations of completed OFF intervals from a [K, n] 0/1 gene-off series."""
-    g = goff.T.astype(np.int8)                        # [n, K]
-    d = np.diff(g, axis=1)                            # +1: switched off, -1: switched on
-    out = []
-    for row in d:
-        starts = np.nonzero(row == 1)[0]
-        ends = np.nonzero(row == -1)[0]
-        j = 0
-        for s0 in starts:
-            while j < len(ends) and ends[j] <= s0:
-                j += 1
-            if j < len(ends):
-                out.append((ends[j] - s0) * dt)
-    return np.array(out)
+def _dwell_stats(h, dt, kon):
+    """Completed OFF intervals from a dwell histogram h[d] (d samples):
+    count, mean duration and the largest gap between their empirical CDF
+    and the exponential law 1 - exp(-kon t) at the observed durations."""
+    d = np.nonzero(h)[0]
+    n = int(h.sum())
+    if n == 0:
+        return {"n_dwells": 0}
+    c = np.cumsum(h)
+    F = 1.0 - np.exp(-kon * d * dt)
+    below = (c[d] - h[d] + 1) / n            # first of the tied samples at d
+    at = c[d] / n                            # last of them
+    ks = float(np.max(np.maximum(np.abs(at - F), np.abs(below - F))))
+    return {"n_dwells": n, "mean": float((h * np.arange(h.size)).sum() * dt / n), "mean_expected": 1.0 / kon,
+            "ks_vs_exponential": ks}
 
 
 def dwell(n_traj=10000, seed=31):
+    """Dwell extraction and the two-sample comparisons run on the device
+    (ssa_dwell_histogram, ssa_hist_ks_w1)."""
     import torch
     from scipy import stats as sst
     kon = 0.05
@@ -250,20 +268,19 @@ def dwell(n_traj=10000, seed=31):
                       ("uniform_bf16", "rn")]:
         r = ssa.ensemble_run(m, n_traj, P.TELEGRAPH_X0, t_end, samples, prec, rnd, False,
                              seed if prec == "fp64" else seed + 1, 10**7)
-        torch.cuda.synchronize()
-        d = _off_dwells(r["snapshots"][:, 0, :].cpu().numpy(), dt)
-        row = {"n_dwells": int(d.size)}
-        if d.size:
-            expo = 1.0 - np.exp(-kon * np.sort(d))
-            emp = np.arange(1, d.size + 1) / d.size
-            row.update({"mean": float(d.mean()), "mean_expected": 1.0 / kon,
-                        "ks_vs_exponential": float(np.max(np.abs(emp - expo)))})
+        h = ssa.dwell_histogram(r["snapshots"], 0)
+        hn = h.cpu().numpy()
+        row = _dwell_stats(hn, dt, kon)
+        if row["n_dwells"]:
             if ref is None:
-                ref = d
+                ref = h
             else:
-                row["ks_p_vs_fp64"] = float(sst.ks_2samp(ref, d).pvalue)
-                row["w1_vs_fp64"] = float(sst.wasserstein_distance(ref, d))
+                D, w1 = (float(v) for v in ssa.hist_ks_w1(ref, h).cpu().numpy())
+                na, nb = int(ref.sum().item()), row["n_dwells"]
+                row["ks_p_vs_fp64"] = float(sst.kstwobign.sf(D * np.sqrt(na * nb / (na + nb))))
+                row["w1_vs_fp64"] = w1 * dt
         out["modes"][f"{prec}:{rnd}"] = row
+        torch.cuda.synchronize()
     return out
 
 

@@ -55,6 +55,9 @@ SIGNATURES = {
     "ssa_surrogate_status": (_I, [_P]),
     "ssa_histogram": (_I, [_P, _I64, _I64, _I, _P, _P]),
     "ssa_hist_w1": (_I, [_P, _P, _I64, _I, _P, _P]),
+    "ssa_count_histogram": (_I, [_P, _I, _I64, _I, _P, _P, _P]),
+    "ssa_hist_ks_w1": (_I, [_P, _P, _I, _P, _P]),
+    "ssa_dwell_histogram": (_I, [_P, _I, _I, _I64, _I64, _P, _P]),
     "ssa_last_error": (ctypes.c_char_p, []),
 }
 
@@ -416,3 +419,52 @@ def hist_w1(p, q, out=None, stream=None):
         out = torch.empty(rows, dtype=torch.float32, device=p.device)
     _check(lib().ssa_hist_w1(_dev_ptr(p), _dev_ptr(q), int(rows), int(bins), _dev_ptr(out), _stream_ptr(stream)))
     return out
+
+
+# ------------------------------------------------------- ensemble statistics
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def count_histogram(values, bins, hist=None, clamped=None, stream=None):
+    """ssa_count_histogram on a contiguous int32/int16 CUDA tensor; returns
+    (hist uint64-as-int64 [bins], clamped [1]) device tensors (accumulated
+    into the given ones, else fresh zeros)."""
+    import torch
+    if values.dtype not in (torch.int32, torch.int16) or not values.is_contiguous():
+        raise ValueError("values must be a contiguous int32 or int16 tensor")
+    if hist is None:
+        hist = torch.zeros(bins, dtype=torch.int64, device=values.device)
+    if clamped is None:
+        clamped = torch.zeros(1, dtype=torch.int64, device=values.device)
+    _check(lib().ssa_count_histogram(_dev_ptr(values), values.element_size(), values.numel(), int(bins),
+                                     _dev_ptr(hist), _dev_ptr(clamped), _stream_ptr(stream)))
+    return hist, clamped
+
+
+def hist_ks_w1(ha, hb, out=None, stream=None):
+    """ssa_hist_ks_w1: device float64 [2] = (KS statistic D, Wasserstein-1)."""
+    import torch
+    if ha.numel() != hb.numel():
+        raise ValueError("histograms must have the same bins")
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=ha.device)
+    _check(lib().ssa_hist_ks_w1(_dev_ptr(ha), _dev_ptr(hb), ha.numel(), _dev_ptr(out), _stream_ptr(stream)))
+    return out
+
+
+def dwell_histogram(snapshots, species, hist=None, stream=None):
+    """ssa_dwell_histogram of species `species` of snapshots [K, N, n]
+    (contiguous CUDA tensor): device int64 [K] of completed OFF-interval lengths."""
+    import torch
+    if not snapshots.is_contiguous() or snapshots.dim() != 3:
+        raise ValueError("snapshots must be a contiguous [K, N, n] tensor")
+    K, N, n = snapshots.shape
+    if hist is None:
+        hist = torch.zeros(K, dtype=torch.int64, device=snapshots.device)
+    base = snapshots[0, species]
+    _check(lib().ssa_dwell_histogram(_dev_ptr(base), snapshots.element_size(), K, n, N * n, _dev_ptr(hist),
+                                     _stream_ptr(stream)))
+    return hist

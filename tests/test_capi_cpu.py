@@ -223,3 +223,18 @@ def test_rdme_run_empty_ensemble_is_a_no_op(ssa):
     rc = ssa.lib().ssa_rdme_run(m.handle, 3, 1, 1, D.ctypes.data, 0, 0, x0.ctypes.data, 1.0, 1, st.ctypes.data,
                                 0, 0, 0, 0, 100, 4, None, None, None, None, None)
     assert rc == ssa.SSA_OK
+
+
+def test_statistics_entry_points_reject_before_launch(ssa):
+    """Argument checks of the ensemble-statistics entry points (no device use)."""
+    L = ssa.lib()
+    fake = ctypes.c_void_p(16)
+    assert L.ssa_count_histogram(fake, 3, 10, 8, fake, fake, None) == ssa.SSA_EINVAL      # element size
+    assert L.ssa_count_histogram(fake, 4, 10, 0, fake, fake, None) == ssa.SSA_EINVAL      # bins
+    assert L.ssa_count_histogram(None, 4, 10, 8, fake, fake, None) == ssa.SSA_EINVAL     # values
+    assert L.ssa_count_histogram(None, 4, 0, 8, None, None, None) == ssa.SSA_OK          # empty
+    assert L.ssa_hist_ks_w1(None, fake, 8, fake, None) == ssa.SSA_EINVAL
+    assert L.ssa_hist_ks_w1(fake, fake, 1 << 25, fake, None) == ssa.SSA_EINVAL
+    assert L.ssa_dwell_histogram(fake, 4, 10, 100, 50, fake, None) == ssa.SSA_EINVAL      # k_stride < n
+    assert L.ssa_dwell_histogram(fake, 4, 0, 100, 100, fake, None) == ssa.SSA_EINVAL      # K
+    assert L.ssa_dwell_histogram(None, 4, 10, 0, 0, None, None) == ssa.SSA_OK

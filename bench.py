@@ -424,6 +424,14 @@ def run_ours(args, world, rank, local):
     modes_out["fp64:rn"] = {"events_per_s": fp64_rate, "ms_per_launch": float(np.mean(fp64_ms)),
                             "mean": float(ref.mean()), "var": float(ref.var())}
 
+    # the metric's KS criterion: which modes of the step match the fp64
+    # ensemble at p > 0.05 (10^4 trajectories of each), and their own rate
+    passing = [m for m in MODES16 if modes_out[f"{m[0]}:{m[1]}"]["ks_p_vs_fp64_n1e4"] > 0.05]
+    pass_ms = sum(sum(kernel_ms[m]) for m in passing)
+    ks_block = {"test": "two-sample KS of X at t_end vs the independent fp64 ensemble, 10^4 trajectories each",
+                "passing_modes": [f"{p}:{r}" for p, r in passing],
+                "events_per_s_passing": (sum(events[m] for m in passing) / (pass_ms / 1e3)) if passing else None}
+
     # roofline of the dominant kernel (largest share of the step)
     dom = max(kernel_ms, key=lambda k: sum(kernel_ms[k]))
     dom_ms = float(np.mean(kernel_ms[dom]))     # on its own stream, inside the timed steps
@@ -446,6 +454,7 @@ def run_ours(args, world, rank, local):
                      "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock sampled in the run)",
                      "snapshot_hbm_gbs": (K_SAMPLES * model.N * N_TRAJ * 4) / (dom_ms / 1e3) / 1e9},
         "fp64_events_per_s": fp64_rate_job, "speedup_vs_fp64": value / fp64_rate_job,
+        "ks_criterion": ks_block,
         "modes": modes_out,
         "e2e": {"value": e2e_events / e2e_time, "unit": "events/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},

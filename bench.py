@@ -503,12 +503,12 @@ RDME_CAP = 4_000_000
 # ncu counts per unit (warp instructions; DRAM bytes), keyed by (device-source
 # hash, workload, mode); a changed kernel reports null until re-counted.
 NCU_PER_UNIT = {
-    # tau, 2e5 trajectories, one launch per mode
-    ("82380294efe007d5", "tau", "fp32:rn"): {"warp_inst": 6.795, "dram_bytes": 0.02867},
-    ("82380294efe007d5", "tau", "mixed_f16:rn"): {"warp_inst": 6.928, "dram_bytes": 0.01969},
-    ("82380294efe007d5", "tau", "mixed_bf16:rn"): {"warp_inst": 6.791, "dram_bytes": 0.01947},
-    ("82380294efe007d5", "tau", "uniform_f16:sr"): {"warp_inst": 7.527, "dram_bytes": 0.02130},
-    ("82380294efe007d5", "tau", "uniform_bf16:sr"): {"warp_inst": 7.396, "dram_bytes": 0.02072},
+    # tau, 2e5 trajectories, one launch per mode (compiled Schloegl structure)
+    ("a38308564600ae6b", "tau", "fp32:rn"): {"warp_inst": 6.301, "dram_bytes": 0.01502},
+    ("a38308564600ae6b", "tau", "mixed_f16:rn"): {"warp_inst": 6.389, "dram_bytes": 0.01537},
+    ("a38308564600ae6b", "tau", "mixed_bf16:rn"): {"warp_inst": 6.270, "dram_bytes": 0.01495},
+    ("a38308564600ae6b", "tau", "uniform_f16:sr"): {"warp_inst": 6.537, "dram_bytes": 0.01181},
+    ("a38308564600ae6b", "tau", "uniform_bf16:sr"): {"warp_inst": 6.438, "dram_bytes": 0.01163},
     # rdme, 32768 lattices, one launch per mode
     ("c0755ae3d51c58b6", "rdme", "fp32:rn"): {"warp_inst": 27.384, "dram_bytes": 0.00012},
     ("c0755ae3d51c58b6", "rdme", "mixed_f16:rn"): {"warp_inst": 29.566, "dram_bytes": 0.00017},
@@ -521,8 +521,8 @@ def ext_source_hash(workload):
     import hashlib
     h = hashlib.sha256()
     files = ["ssa_device.cuh", "ssa_models.h", "ssa_launch.h"]
-    files += ["tau_device.cuh", "ssa_k_tau.cu"] if workload == "tau" else ["rdme_device.cuh", "ssa_k_rdme.cu",
-                                                                          "ssa_k_rdme_schlogl.cu"]
+    files += (["tau_device.cuh", "tau_launch.h", "ssa_k_tau.cu", "ssa_k_tau_schlogl.cu"] if workload == "tau" else
+              ["rdme_device.cuh", "ssa_k_rdme.cu", "ssa_k_rdme_schlogl.cu"])
     for f in files:
         with open(os.path.join(ROOT, "paper_2605_00479_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())

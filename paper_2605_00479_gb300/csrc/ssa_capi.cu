@@ -19,6 +19,7 @@
 #include "../../include/ssa.h"
 #include "rdme_device.cuh"
 #include "ssa_launch.h"
+#include "tau_launch.h"
 #include "ssa_models.h"
 
 struct ssa_model {
@@ -586,7 +587,7 @@ int ssa_tau_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, co
     }
     a->queue_head = head;
     int grid = 0;
-    e = ssa::launch_tau(*a, precision, rounding, g_cfg, s, &grid);
+    e = ssa::launch_tau_family(*a, model->family, normalise ? 1 : 0, precision, rounding, g_cfg, s, &grid);
     cudaError_t e2 = cudaFreeAsync(head, s);
     delete a;
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");

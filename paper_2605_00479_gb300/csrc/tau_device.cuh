@@ -19,6 +19,8 @@
 //    status TAU_CLAMPED (16); the event count is sum_j k_j.
 #pragma once
 
+#include <type_traits>
+
 #include "ssa_device.cuh"
 
 namespace ssa {
@@ -130,7 +132,7 @@ struct SamplerWords {
     }
 };
 
-__device__ int64_t poisson_f32(float lam, SamplerWords &s)
+__device__ inline int64_t poisson_f32(float lam, SamplerWords &s)
 {
     if (!(lam > 0.0f)) return 0;
     if (lam < 10.0f) {
@@ -175,7 +177,7 @@ __device__ int64_t poisson_f32(float lam, SamplerWords &s)
     return (int64_t)floorf(lam);
 }
 
-__device__ int64_t poisson_f64(double lam, SamplerWords &s)
+__device__ inline int64_t poisson_f64(double lam, SamplerWords &s)
 {
     if (!(lam > 0.0)) return 0;
     if (lam < 10.0) {
@@ -220,11 +222,11 @@ __device__ int64_t poisson_f64(double lam, SamplerWords &s)
     return (int64_t)floor(lam);
 }
 
-template <int PREC>
-__device__ void tau_finish(const RunArgs &a, Lane<GeneralModel, PREC> &L)
+template <class Model, int PREC>
+__device__ void tau_finish(const RunArgs &a, Lane<Model, PREC> &L)
 {
     while (L.k < a.K) {
-        store_state<GeneralModel>(a, L.k, L.item, L.x, L.status);
+        store_state<Model>(a, L.k, L.item, L.x, L.status);
         L.k += 1;
     }
     a.status[L.item] = L.status;
@@ -233,85 +235,180 @@ __device__ void tau_finish(const RunArgs &a, Lane<GeneralModel, PREC> &L)
     L.active = false;
 }
 
+// Propensities of a compiled structure: the direct method's chain (the same
+// operations and rounding slots as general_propensities), unrolled.
+template <class Model, int PREC, int SR>
+__device__ __forceinline__ void static_propensities(const RunArgs &a, const Lane<Model, PREC> &L,
+                                                    Rounder<PREC, SR> &R, typename ModeTraits<PREC>::P *prop)
+{
+    using P = typename ModeTraits<PREC>::P;
+    unroll<Model::M>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        int op = Model::template chain_start<j>(a);
+        if (Model::template law<j>(a) == 1) {
+            const int reg = Model::template hill_reg<j>(a);
+            int xr = 0;
+            unroll<Model::N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                if (i == reg) xr = L.x[i];
+            });
+            const P Pv = R.rnd((P)xr, op++);
+            P q = Pv;
+            const int h = Model::template hill_h<j>(a);
+            for (int m = 1; m < h; ++m) q = R.rnd(q * Pv, op++);
+            const P d = R.rnd(P(1) + q, op++);
+            const P f = R.rnd(L.h1[j] / d, op++);
+            prop[j] = R.rnd(L.h0[j] + f, op++);
+        } else {
+            P av = L.c[j];
+            bool zero = false;
+            unroll<Model::N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const int rr = Model::template order<j, i>(a);
+                if (rr > 0 && !Model::template folded<j, i>(a)) {
+                    zero = zero || (L.x[i] < rr);
+                    for (int m = 0; m < rr; ++m) {
+                        const P f = R.rnd((P)(L.x[i] - m), op++);
+                        av = R.rnd(av * f, op++);
+                    }
+                }
+            });
+            prop[j] = zero ? P(0) : av;
+        }
+    });
+}
+
+// Out-of-line sampler call for the unrolled channel loop of compiled
+// structures (one copy of the sampler instead of one per channel).
+template <int PREC>
+__device__ __noinline__ int64_t poisson_call(typename ModeTraits<PREC>::P lam, SamplerWords &s)
+{
+    if constexpr (ModeTraits<PREC>::kF64) return poisson_f64(lam, s);
+    else return poisson_f32(lam, s);
+}
+
 // One leap n = L.n of an active lane.
-template <int PREC, int SR>
-__device__ __noinline__ void tau_leap(const RunArgs &a, Lane<GeneralModel, PREC> &L, const double *smp)
+template <class Model, int PREC, int SR>
+__device__ __noinline__ void tau_leap(const RunArgs &a, Lane<Model, PREC> &L, const double *smp)
 {
     using Tr = ModeTraits<PREC>;
     using P = typename Tr::P;
+    constexpr bool kGeneral = std::is_same<Model, GeneralModel>::value;
     const int64_t n = L.n;
     const double t_next = (double)(n + 1) * a.tau;
     while (L.k < a.K && smp[L.k] < t_next) {
-        store_state<GeneralModel>(a, L.k, L.item, L.x, L.status);
+        store_state<Model>(a, L.k, L.item, L.x, L.status);
         L.k += 1;
     }
     Rounder<PREC, SR> R;
     if constexpr (Tr::k16 && SR) {
-        const int sr_total = a.sr_ops + (Tr::kUniform ? a.M : 0);
+        const int sr_total = Model::total_chain_ops(a) + (Tr::kUniform ? Model::last(a) + 1 : 0);
         R.bits.base = (uint64_t)n * (uint64_t)((sr_total + 7) >> 3);
         R.bits.traj = L.traj;
         R.bits.k0 = a.key0;
         R.bits.k1 = a.key1;
         R.bits.cur = -1;
     }
-    P prop[kMaxM];
-    general_propensities<PREC, SR>(a, L, R, prop);
-    P lam[kMaxM];
-    uint32_t bad = 0;
     const float tau32 = (float)a.tau;
     float tau16 = tau32;
     if constexpr (Tr::k16) tau16 = rn16<Tr::kFmt>(tau32);
+    const int lam_op = Model::total_chain_ops(a);   // SR slot of lambda_0 (uniform modes)
+    auto lambda_of = [&](P prop, int j) -> P {
+        if constexpr (Tr::kF64) return prop * a.tau;
+        else if constexpr (Tr::kUniform) return R.rnd(prop * tau16, lam_op + j);
+        else return prop * tau32;
+    };
+    P prop[Model::M];
+    P lam[Model::M];
+    uint32_t bad = 0;
+    if constexpr (kGeneral) {
+        general_propensities<PREC, SR>(a, L, R, prop);
 #pragma unroll 1
-    for (int j = 0; j < a.M; ++j) {
-        P v;
-        if constexpr (Tr::kF64) v = prop[j] * a.tau;
-        else if constexpr (Tr::kUniform) v = R.rnd(prop[j] * tau16, a.sr_ops + j);
-        else v = prop[j] * tau32;
-        lam[j] = v;
-        if (v != v) bad |= ST_NAN;
-        else if (v == P(__int_as_float(0x7F800000))) bad |= ST_OVERFLOW;
+        for (int j = 0; j < a.M; ++j) {
+            const P v = lambda_of(prop[j], j);
+            lam[j] = v;
+            if (v != v) bad |= ST_NAN;
+            else if (v == P(__int_as_float(0x7F800000))) bad |= ST_OVERFLOW;
+        }
+    } else {
+        static_propensities<Model, PREC, SR>(a, L, R, prop);
+        unroll<Model::M>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            const P v = lambda_of(prop[j], j);
+            lam[j] = v;
+            if (v != v) bad |= ST_NAN;
+            else if (v == P(__int_as_float(0x7F800000))) bad |= ST_OVERFLOW;
+        });
     }
     if (bad) {
         L.status |= bad;
-        tau_finish<PREC>(a, L);
+        tau_finish<Model, PREC>(a, L);
         return;
     }
-    int64_t dx[kMaxN];
+    int64_t dx[Model::N];
 #pragma unroll
-    for (int i = 0; i < kMaxN; ++i) dx[i] = 0;
+    for (int i = 0; i < Model::N; ++i) dx[i] = 0;
+    SamplerWords sw;
+    sw.k0 = a.key0;
+    sw.k1 = a.key1;
+    sw.leap = (uint32_t)n;
+    sw.traj = L.traj;
+    if constexpr (kGeneral) {
 #pragma unroll 1
-    for (int j = 0; j < a.M; ++j) {
-        SamplerWords sw;
-        sw.k0 = a.key0;
-        sw.k1 = a.key1;
-        sw.leap = (uint32_t)n;
-        sw.traj = L.traj;
-        sw.stream = 2u + (uint32_t)j;
-        sw.w = 0;
-        int64_t kj;
-        if constexpr (Tr::kF64) kj = poisson_f64(lam[j], sw);
-        else kj = poisson_f32(lam[j], sw);
-        L.ev += kj;
+        for (int j = 0; j < a.M; ++j) {
+            sw.stream = 2u + (uint32_t)j;
+            sw.w = 0;
+            int64_t kj;
+            if constexpr (Tr::kF64) kj = poisson_f64(lam[j], sw);
+            else kj = poisson_f32(lam[j], sw);
+            L.ev += kj;
 #pragma unroll 1
-        for (int i = 0; i < a.N; ++i) dx[i] += kj * (int64_t)a.stoich[j][i];
-    }
-#pragma unroll 1
-    for (int i = 0; i < a.N; ++i) {
-        int64_t v = (int64_t)L.x[i] + dx[i];
-        if (v < 0) {
-            v = 0;
-            L.status |= ST_TAU_CLAMPED;
+            for (int i = 0; i < a.N; ++i) dx[i] += kj * (int64_t)a.stoich[j][i];
         }
-        if (v > 2147483647) v = 2147483647;
-        L.x[i] = (int)v;
+    } else {
+        unroll<Model::M>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            sw.stream = 2u + (uint32_t)j;
+            sw.w = 0;
+            const int64_t kj = poisson_call<PREC>(lam[j], sw);
+            L.ev += kj;
+            unroll<Model::N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const int nu = Model::template nu<j, i>(a);
+                if (nu != 0) dx[i] += kj * (int64_t)nu;
+            });
+        });
+    }
+    if constexpr (kGeneral) {
+#pragma unroll 1
+        for (int i = 0; i < a.N; ++i) {
+            int64_t v = (int64_t)L.x[i] + dx[i];
+            if (v < 0) {
+                v = 0;
+                L.status |= ST_TAU_CLAMPED;
+            }
+            if (v > 2147483647) v = 2147483647;
+            L.x[i] = (int)v;
+        }
+    } else {
+        unroll<Model::N>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            int64_t v = (int64_t)L.x[i] + dx[i];
+            if (v < 0) {
+                v = 0;
+                L.status |= ST_TAU_CLAMPED;
+            }
+            if (v > 2147483647) v = 2147483647;
+            L.x[i] = (int)v;
+        });
     }
     L.n = n + 1;
-    if (L.n >= a.n_leaps) tau_finish<PREC>(a, L);
+    if (L.n >= a.n_leaps) tau_finish<Model, PREC>(a, L);
 }
-
-// Persistent tau-leaping kernel (general model tables): lanes refill from the
-// work queue as in the direct method; each loop iteration runs one leap.
-template <int PREC, int SR>
+// Persistent tau-leaping kernel: lanes refill from the work queue as in the
+// direct method; each loop iteration runs one leap.  Model is a compiled
+// structure (StaticModel) or the runtime-table GeneralModel.
+template <class Model, int PREC, int SR>
 __global__ void __launch_bounds__(256) tau_kernel(const __grid_constant__ RunArgs a)
 {
     using P = typename ModeTraits<PREC>::P;
@@ -320,7 +417,7 @@ __global__ void __launch_bounds__(256) tau_kernel(const __grid_constant__ RunArg
     __syncthreads();
     const unsigned lane = threadIdx.x & 31u;
     const P no_samples[1] = {P(0)};
-    Lane<GeneralModel, PREC> L;
+    Lane<Model, PREC> L;
     L.active = false;
     bool drained = false;
     for (;;) {
@@ -333,17 +430,52 @@ __global__ void __launch_bounds__(256) tau_kernel(const __grid_constant__ RunArg
             if (!L.active && !drained) {
                 const unsigned long long item = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
                 if (item < (unsigned long long)a.n_work) {
-                    init_lane<GeneralModel, PREC>(a, L, (int64_t)item, no_samples);
+                    init_lane<Model, PREC>(a, L, (int64_t)item, no_samples);
                     L.ev = 0;
-                    if (a.n_leaps <= 0) tau_finish<PREC>(a, L);
+                    if (a.n_leaps <= 0) tau_finish<Model, PREC>(a, L);
                 } else {
                     drained = true;
                 }
             }
         }
         if (__ballot_sync(0xFFFFFFFFu, L.active) == 0u) break;
-        if (L.active) tau_leap<PREC, SR>(a, L, smp);
+        if (L.active) tau_leap<Model, PREC, SR>(a, L, smp);
     }
+}
+
+// Launch of one structure's kernel for (precision, rounding); the grid is
+// sized from occupancy (persistent), capped by the work.
+template <class Model>
+cudaError_t tau_launch_model(const RunArgs &a, int prec, int sr, int block, int blocks_per_sm, cudaStream_t stream,
+                             int *grid_out)
+{
+    using K = void (*)(const RunArgs);
+    K k = nullptr;
+    switch (prec) {
+    case FP64: k = tau_kernel<Model, FP64, 0>; break;
+    case FP32: k = tau_kernel<Model, FP32, 0>; break;
+    case MIXED_F16: k = sr ? tau_kernel<Model, MIXED_F16, 1> : tau_kernel<Model, MIXED_F16, 0>; break;
+    case MIXED_BF16: k = sr ? tau_kernel<Model, MIXED_BF16, 1> : tau_kernel<Model, MIXED_BF16, 0>; break;
+    case UNIFORM_F16: k = sr ? tau_kernel<Model, UNIFORM_F16, 1> : tau_kernel<Model, UNIFORM_F16, 0>; break;
+    case UNIFORM_BF16: k = sr ? tau_kernel<Model, UNIFORM_BF16, 1> : tau_kernel<Model, UNIFORM_BF16, 0>; break;
+    default: return cudaErrorInvalidValue;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+    long long grid = (long long)sms * per_sm;
+    const long long need = (a.n_work + block - 1) / block;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    *grid_out = (int)grid;
+    k<<<(unsigned)grid, (unsigned)block, 0, stream>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace ssa

@@ -91,8 +91,9 @@ def ops_per_event(prec, rnd):
 # trajectories).  Valid only for the kernel source it was measured on: the
 # key includes a hash of the device code, and a changed kernel reports null.
 NCU_TRAFFIC_PER_TRAJ = {
-    # uniform_f16 RN, 3e5 trajectories: 274,445,824 B read + 447,058,944 B written
-    ("2f0c5b3a6f0732d0", "uniform_f16:rn"): (274445824 + 447058944) / 300000,
+    # uniform_f16 RN, 3e5 trajectories, default launch shape (128 threads, 16 step
+    # pairs per refill check): 277,933,312 B read + 446,081,280 B written
+    ("2f0c5b3a6f0732d0", "uniform_f16:rn"): (277933312 + 446081280) / 300000,
 }
 
 

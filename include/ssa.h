@@ -250,6 +250,8 @@ int ssa_rdme_run(const ssa_model *model, int nx, int ny, int nz, const double *d
  *                      occupancy calculator allows)
  *   slice_pairs        pairs of steps each lane runs between two checks for
  *                      finished lanes to refill, 1..64
+ * The library starts at (128, 0, 16).  Tau-leaping and RDME kernels take the
+ * block size from here and always check for refills after every step.
  * Results never depend on the launch shape; only speed does.  Not
  * synchronised with concurrent launches from other threads.
  * Errors: SSA_EINVAL.

@@ -53,7 +53,7 @@ int cuda_fail(cudaError_t e, const char *what)
     return fail(SSA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-ssa::LaunchConfig g_cfg = {128, 0, 1};
+ssa::LaunchConfig g_cfg = {128, 0, 16};   // library default launch shape
 
 template <class S>
 bool matches(const ssa_model &m)

@@ -139,8 +139,9 @@ class Model:
             pass
 
 
-def set_launch_config(threads_per_block=128, blocks_per_sm=0, slice_pairs=1):
-    """Launch shape for later runs (speed only; results do not depend on it)."""
+def set_launch_config(threads_per_block=128, blocks_per_sm=0, slice_pairs=16):
+    """Launch shape for later runs (speed only; results do not depend on it).
+    The defaults are the library's own starting shape."""
     _check(lib().ssa_set_launch_config(int(threads_per_block), int(blocks_per_sm), int(slice_pairs)))
 
 

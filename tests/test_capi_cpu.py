@@ -113,7 +113,7 @@ def test_launch_config_validation(ssa):
         ssa.set_launch_config(48, 0, 1)
     with pytest.raises(ssa.SSAError):
         ssa.set_launch_config(512, 0, 1)
-    ssa.set_launch_config(128, 0, 1)
+    ssa.set_launch_config()
 
 
 def test_batch_create_rejects_before_allocating(ssa):

@@ -131,7 +131,7 @@ def test_rdme_ragged_offset_int16_and_launch_shape(ssa):
             assert g["snapshots"].dtype == np.int16
             assert_same(g, o)
     finally:
-        ssa.set_launch_config(128, 0, 1)
+        ssa.set_launch_config()
 
 
 def test_rdme_event_cap_and_overflow(ssa):

@@ -135,7 +135,7 @@ def test_tau_ragged_offset_int16_and_launch_shape(ssa):
             assert g["snapshots"].dtype == np.int16
             assert_same(g, o)
     finally:
-        ssa.set_launch_config(128, 0, 1)
+        ssa.set_launch_config()
 
 
 def test_tau_single_leap_and_off_grid_end(ssa):

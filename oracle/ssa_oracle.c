@@ -495,13 +495,19 @@ static void write_snapshot(const sink *S, int k, const int32_t *x, uint32_t *sta
     }
 }
 
-static void apply_event(const omodel *md, int mu, int32_t *x, uint32_t *status)
+/* Returns 1 when a count went negative (the trajectory ends: R9).  The
+ * STATE_RANGE bit alone does not end it: int16 snapshot storage sets the same
+ * bit when it clamps, and storage never changes a trajectory. */
+static int apply_event(const omodel *md, int mu, int32_t *x, uint32_t *status)
 {
+    int negative = 0;
     for (int i = 0; i < md->N; ++i) {
         if (md->constant && md->constant[i]) continue;
         x[i] += md->stoich[mu * md->N + i];
-        if (x[i] < 0) *status |= ST_STATE_RANGE;
+        if (x[i] < 0) negative = 1;
     }
+    if (negative) *status |= ST_STATE_RANGE;
+    return negative;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -549,10 +555,10 @@ static void traj_f64(const omodel *md, const runp *rp, word_stream *ws, int32_t 
         int mu = -1;
         for (int j = 0; j < M; ++j) if (Ssum[j] > target) { mu = j; break; }
         if (mu < 0) for (int j = M - 1; j >= 0; --j) if (a[j] > 0.0) { mu = j; break; }
-        apply_event(md, mu, x, status);
+        const int negative = apply_event(md, mu, x, status);
         t = t_new;
         n += 1;
-        if (*status & ST_STATE_RANGE) break;
+        if (negative) break;
     }
     while (k < rp->K) write_snapshot(S, k++, x, status);
     *n_events = n;
@@ -610,10 +616,10 @@ static void traj_f32_mixed(const omodel *md, const runp *rp, word_stream *ws, wo
         int mu = -1;
         for (int j = 0; j < M; ++j) if (Ssum[j] > target) { mu = j; break; }
         if (mu < 0) for (int j = M - 1; j >= 0; --j) if (a[j] > 0.0f) { mu = j; break; }
-        apply_event(md, mu, x, status);
+        const int negative = apply_event(md, mu, x, status);
         t = t_new;
         n += 1;
-        if (*status & ST_STATE_RANGE) break;
+        if (negative) break;
     }
     while (k < rp->K) write_snapshot(S, k++, x, status);
     *n_events = n;
@@ -676,10 +682,10 @@ static void traj_uniform(const omodel *md, const runp *rp, word_stream *ws, word
         int mu = -1;
         for (int j = 0; j < M; ++j) if (Ssum[j] > target) { mu = j; break; }
         if (mu < 0) for (int j = M - 1; j >= 0; --j) if (a[j] > 0.0f) { mu = j; break; }
-        apply_event(md, mu, x, status);
+        const int negative = apply_event(md, mu, x, status);
         t = t_new;
         n += 1;
-        if (*status & ST_STATE_RANGE) break;
+        if (negative) break;
     }
     while (k < rp->K) write_snapshot(S, k++, x, status);
     *n_events = n;
@@ -1351,19 +1357,25 @@ static void set_tag(word_stream *ws, uint32_t tag)
     ws->have = 0;
 }
 
-/* Apply channel c of voxel v; returns the second changed voxel (hop) or -1. */
-static int rdme_apply(const omodel *md, const olattice *L, int v, int c, int32_t *x, uint32_t *status)
+/* Apply channel c of voxel v; returns the second changed voxel (hop) or -1.
+ * *negative = 1 when a count went negative (the trajectory ends). */
+static int rdme_apply(const omodel *md, const olattice *L, int v, int c, int32_t *x, uint32_t *status,
+                      int *negative)
 {
     const int N = md->N;
+    *negative = 0;
     if (c < md->M) {
-        apply_event(md, c, x + v * N, status);
+        *negative = apply_event(md, c, x + v * N, status);
         return -1;
     }
     int i, w;
     hop_channel(md, L, v, c, &i, &w);
     x[v * N + i] -= 1;
     x[w * N + i] += 1;
-    if (x[v * N + i] < 0) *status |= ST_STATE_RANGE;
+    if (x[v * N + i] < 0) {
+        *status |= ST_STATE_RANGE;
+        *negative = 1;
+    }
     return w;
 }
 
@@ -1410,10 +1422,11 @@ static void rdme_traj_f64(const omodel *md, const olattice *L, const runp *rp, w
         int v = q - T, c = -1;
         voxel_f64(md, L, x + v * N, v, cp, h0, h1, r, &c);
         if (c < 0) { *status |= ST_NAN; break; }   /* unreachable: the descent only enters positive totals */
-        int w2 = rdme_apply(md, L, v, c, x, status);
+        int negative = 0;
+        int w2 = rdme_apply(md, L, v, c, x, status, &negative);
         t = t_new;
         n += 1;
-        if (*status & ST_STATE_RANGE) break;
+        if (negative) break;
         node[T + v] = voxel_f64(md, L, x + v * N, v, cp, h0, h1, 0.0, NULL);
         if (w2 >= 0) node[T + w2] = voxel_f64(md, L, x + w2 * N, w2, cp, h0, h1, 0.0, NULL);
         /* ancestors, level by level; qb = 0 once the two paths have merged */
@@ -1529,10 +1542,11 @@ static void rdme_traj_f32(const omodel *md, const olattice *L, const runp *rp, w
         int v = q - T, c = -1;
         voxel_at_f32(md, L, x, v, epoch[v], cp, h0, h1, Dp, kind, fmt, sr, wsv, r, &c);
         if (c < 0) { *status |= ST_NAN; break; }   /* unreachable: the descent only enters positive totals */
-        int w2 = rdme_apply(md, L, v, c, x, status);
+        int negative = 0;
+        int w2 = rdme_apply(md, L, v, c, x, status, &negative);
         t = t_new;
         n += 1;
-        if (*status & ST_STATE_RANGE) break;
+        if (negative) break;
         const uint32_t e = (uint32_t)n;            /* epoch n + 1 of the event just applied */
         node[T + v] = voxel_at_f32(md, L, x, v, e, cp, h0, h1, Dp, kind, fmt, sr, wsv, 0.0f, NULL);
         epoch[v] = e;

@@ -91,9 +91,9 @@ def ops_per_event(prec, rnd):
 # trajectories).  Valid only for the kernel source it was measured on: the
 # key includes a hash of the device code, and a changed kernel reports null.
 NCU_TRAFFIC_PER_TRAJ = {
-    # uniform_f16 RN, 3e5 trajectories, default launch shape (128 threads, 16 step
-    # pairs per refill check): 277,933,312 B read + 446,081,280 B written
-    ("2f0c5b3a6f0732d0", "uniform_f16:rn"): (277933312 + 446081280) / 300000,
+    # uniform_f16 RN, 3e5 trajectories, default launch shape (256 threads, 32 step
+    # pairs per refill check, tail compaction): 265,567,232 B read + 437,347,840 B written
+    ("5b5016d9bc542804", "uniform_f16:rn"): (265567232 + 437347840) / 300000,
 }
 
 
@@ -505,16 +505,16 @@ RDME_CAP = 4_000_000
 # hash, workload, mode); a changed kernel reports null until re-counted.
 NCU_PER_UNIT = {
     # tau, 2e5 trajectories, one launch per mode (compiled Schloegl structure)
-    ("a38308564600ae6b", "tau", "fp32:rn"): {"warp_inst": 6.301, "dram_bytes": 0.01502},
-    ("a38308564600ae6b", "tau", "mixed_f16:rn"): {"warp_inst": 6.389, "dram_bytes": 0.01537},
-    ("a38308564600ae6b", "tau", "mixed_bf16:rn"): {"warp_inst": 6.270, "dram_bytes": 0.01495},
-    ("a38308564600ae6b", "tau", "uniform_f16:sr"): {"warp_inst": 6.537, "dram_bytes": 0.01181},
-    ("a38308564600ae6b", "tau", "uniform_bf16:sr"): {"warp_inst": 6.438, "dram_bytes": 0.01163},
+    ("23f73587f1d6b961", "tau", "fp32:rn"): {"warp_inst": 6.301, "dram_bytes": 0.01498},
+    ("23f73587f1d6b961", "tau", "mixed_f16:rn"): {"warp_inst": 6.389, "dram_bytes": 0.01513},
+    ("23f73587f1d6b961", "tau", "mixed_bf16:rn"): {"warp_inst": 6.270, "dram_bytes": 0.01506},
+    ("23f73587f1d6b961", "tau", "uniform_f16:sr"): {"warp_inst": 6.537, "dram_bytes": 0.01197},
+    ("23f73587f1d6b961", "tau", "uniform_bf16:sr"): {"warp_inst": 6.438, "dram_bytes": 0.01148},
     # rdme, 32768 lattices, one launch per mode
-    ("c0755ae3d51c58b6", "rdme", "fp32:rn"): {"warp_inst": 27.384, "dram_bytes": 0.00012},
-    ("c0755ae3d51c58b6", "rdme", "mixed_f16:rn"): {"warp_inst": 29.566, "dram_bytes": 0.00017},
-    ("c0755ae3d51c58b6", "rdme", "mixed_bf16:rn"): {"warp_inst": 29.552, "dram_bytes": 0.00063},
-    ("c0755ae3d51c58b6", "rdme", "mixed_f16:sr"): {"warp_inst": 40.192, "dram_bytes": 0.00114},
+    ("b1d849b6bfc208b5", "rdme", "fp32:rn"): {"warp_inst": 27.384, "dram_bytes": 0.00015},
+    ("b1d849b6bfc208b5", "rdme", "mixed_f16:rn"): {"warp_inst": 29.566, "dram_bytes": 0.00021},
+    ("b1d849b6bfc208b5", "rdme", "mixed_bf16:rn"): {"warp_inst": 29.552, "dram_bytes": 0.00066},
+    ("b1d849b6bfc208b5", "rdme", "mixed_f16:sr"): {"warp_inst": 40.192, "dram_bytes": 0.00112},
 }
 
 

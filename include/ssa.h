@@ -250,13 +250,41 @@ int ssa_rdme_run(const ssa_model *model, int nx, int ny, int nz, const double *d
  *                      occupancy calculator allows)
  *   slice_pairs        pairs of steps each lane runs between two checks for
  *                      finished lanes to refill, 1..64
- * The library starts at (128, 0, 16).  Tau-leaping and RDME kernels take the
- * block size from here and always check for refills after every step.
+ * threads_per_block = 0 restores the library's defaults (the other arguments
+ * are then ignored): (256, 0, 32) for single-queue direct-method runs and
+ * (128, 0, 16) for tau-leaping, RDME and batches, the fastest measured for
+ * each.  Once a shape is set, every kind of run uses it.  Tau-leaping and
+ * RDME kernels take only the block size and check for refills after every
+ * step.
  * Results never depend on the launch shape; only speed does.  Not
  * synchronised with concurrent launches from other threads.
  * Errors: SSA_EINVAL.
  */
 int ssa_set_launch_config(int threads_per_block, int blocks_per_sm, int slice_pairs);
+
+/*
+ * ssa_set_tail_compaction -- tail compaction for subsequent direct-method
+ * runs (ssa_ensemble_run, ssa_ensemble_run_host, ssa_sweep_run_noalloc):
+ * 1 (the default) or 0.  Once the work queue has drained, a warp whose
+ * unfinished trajectories fit into the idle lanes of the other warps of its
+ * block hands them over (through shared memory) and stops, so the last
+ * trajectories of a launch run on fewer, fuller warps.  A trajectory's state
+ * moves whole, so results never depend on this; only speed does.  No paper
+ * counterpart (the paper runs trajectories one after another on a CPU).
+ * Errors: SSA_EINVAL.
+ */
+int ssa_set_tail_compaction(int enabled);
+
+/*
+ * ssa_tail_stats -- synchronises the current device, then reports, for all
+ * direct-method launches of this process on it so far, the trajectories moved
+ * between warps by tail compaction (*moved) and the hand-off lock waits that
+ * gave up (*lock_timeouts; each wait is bounded, under a second).  A nonzero
+ * *lock_timeouts means a launch may have left trajectories unfinished: treat
+ * its outputs as invalid.  Either pointer may be NULL.
+ * Errors: SSA_ECUDA.
+ */
+int ssa_tail_stats(int64_t *moved, int64_t *lock_timeouts);
 
 /*
  * Batched heterogeneous runs: several groups, each a model with a sweep of

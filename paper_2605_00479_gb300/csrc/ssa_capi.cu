@@ -53,7 +53,37 @@ int cuda_fail(cudaError_t e, const char *what)
     return fail(SSA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-ssa::LaunchConfig g_cfg = {128, 0, 16};   // library default launch shape
+// Launch shapes.  Until ssa_set_launch_config is called, single-queue
+// direct-method runs use kDirectDefault and tau-leaping, RDME and batches use
+// kOtherDefault (each the fastest measured for its kernels); afterwards all
+// use the shape that was set.
+constexpr ssa::LaunchConfig kDirectDefault = {256, 0, 32};
+constexpr ssa::LaunchConfig kOtherDefault = {128, 0, 16};
+ssa::LaunchConfig g_cfg = kDirectDefault;
+bool g_cfg_set = false;
+
+ssa::LaunchConfig other_cfg() { return g_cfg_set ? g_cfg : kOtherDefault; }
+bool g_tail_compaction = true;
+
+}  // namespace
+
+// Counters of the direct-method kernels' tail compaction on each device:
+// [0] trajectories moved between warps, [1] lock waits that gave up.
+__device__ unsigned long long g_tail_counters[2];
+
+namespace {
+
+// Device address of this device's counters, or null when compaction is off.
+unsigned long long *tail_counters()
+{
+    if (!g_tail_compaction) return nullptr;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tail_counters) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return static_cast<unsigned long long *>(p);
+}
 
 template <class S>
 bool matches(const ssa_model &m)
@@ -235,6 +265,7 @@ int launch_run(const ssa_model *model, int64_t n_work, int64_t stride, uint64_t 
         return cuda_fail(e, "cudaMemsetAsync");
     }
     a->queue_head = head;
+    a->tail_stats = tail_counters();
     int grid = 0;
     e = launcher_for(model->family)(*a, precision, rounding, normalise ? 1 : 0, g_cfg, s, &grid);
     cudaError_t e2 = cudaFreeAsync(head, s);
@@ -252,13 +283,37 @@ const char *ssa_last_error(void) { return g_last_error.c_str(); }
 
 int ssa_set_launch_config(int threads_per_block, int blocks_per_sm, int slice_pairs)
 {
+    if (threads_per_block == 0) {   // back to the library's defaults
+        g_cfg = kDirectDefault;
+        g_cfg_set = false;
+        return SSA_OK;
+    }
     if (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32 != 0)
         return fail(SSA_EINVAL, "threads_per_block must be a multiple of 32 in 32..256");
     if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(SSA_EINVAL, "blocks_per_sm must be in 0..64");
     if (slice_pairs < 1 || slice_pairs > 64) return fail(SSA_EINVAL, "slice_pairs must be in 1..64");
+    g_cfg_set = true;
     g_cfg.block = threads_per_block;
     g_cfg.blocks_per_sm = blocks_per_sm;
     g_cfg.slice_pairs = slice_pairs;
+    return SSA_OK;
+}
+
+int ssa_set_tail_compaction(int enabled)
+{
+    if (enabled != 0 && enabled != 1) return fail(SSA_EINVAL, "enabled must be 0 or 1");
+    g_tail_compaction = enabled != 0;
+    return SSA_OK;
+}
+
+int ssa_tail_stats(int64_t *moved, int64_t *lock_timeouts)
+{
+    unsigned long long c[2] = {0, 0};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(c, g_tail_counters, sizeof(c));
+    if (e != cudaSuccess) return cuda_fail(e, "tail counters");
+    if (moved) *moved = (int64_t)c[0];
+    if (lock_timeouts) *lock_timeouts = (int64_t)c[1];
     return SSA_OK;
 }
 
@@ -499,7 +554,7 @@ int ssa_rdme_run(const ssa_model *model, int nx, int ny, int nz, const double *d
     A->a.t_final = t_final;
     const int elem = precision == SSA_FP64 ? 8 : 4;
     const bool epochs = precision >= SSA_MIXED_F16 && rounding == SSA_SR;
-    if (ssa::rdme_block_size(*A, elem, epochs, g_cfg.block) < 32) {
+    if (ssa::rdme_block_size(*A, elem, epochs, other_cfg().block) < 32) {
         delete A;
         return fail(SSA_EINVAL, "lattice state of %lld voxels x %d species does not fit in shared memory", S, N);
     }
@@ -526,7 +581,7 @@ int ssa_rdme_run(const ssa_model *model, int nx, int ny, int nz, const double *d
         return cuda_fail(e, "RDME table upload");
     }
     int grid = 0, block = 0;
-    e = ssa::launch_rdme(*A, model->family, normalise ? 1 : 0, precision, rounding, g_cfg, s, &grid, &block);
+    e = ssa::launch_rdme(*A, model->family, normalise ? 1 : 0, precision, rounding, other_cfg(), s, &grid, &block);
     cudaError_t e2 = cudaFreeAsync(d, s);
     delete A;
     if (e != cudaSuccess) return cuda_fail(e, "RDME kernel launch");
@@ -587,7 +642,7 @@ int ssa_tau_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, co
     }
     a->queue_head = head;
     int grid = 0;
-    e = ssa::launch_tau_family(*a, model->family, normalise ? 1 : 0, precision, rounding, g_cfg, s, &grid);
+    e = ssa::launch_tau_family(*a, model->family, normalise ? 1 : 0, precision, rounding, other_cfg(), s, &grid);
     cudaError_t e2 = cudaFreeAsync(head, s);
     delete a;
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -711,7 +766,7 @@ int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, 
     b->normalise = normalise ? 1 : 0;
     b->compact = compact;
     b->work = work;
-    b->cfg = g_cfg;
+    b->cfg = other_cfg();
     b->h_groups = new (std::nothrow) ssa::RunArgs[n_groups];
     b->args = new (std::nothrow) ssa::BatchArgs;
     if (!b->h_groups || !b->args) {
@@ -1067,6 +1122,7 @@ int ssa_sweep_run_noalloc(const ssa_model *model, int64_t n_sets, int64_t traj_p
     a.n_events = n_events;
     a.t_final = t_final;
     a.queue_head = head;
+    a.tail_stats = tail_counters();
 
     // the scratch keeps the previous call's contents: reset the queue counter
     cudaError_t e = cudaMemsetAsync(head, 0, sizeof(unsigned long long), s);

@@ -96,6 +96,7 @@ struct RunArgs {
     int64_t *n_events;
     double *t_final;
     unsigned long long *queue_head;    // zero before launch
+    unsigned long long *tail_stats;    // [trajectories moved, lock waits given up]; null: no tail compaction
 };
 
 // ------------------------------------------------------------------ Philox
@@ -869,15 +870,200 @@ __device__ __noinline__ void ssa_step_general(const RunArgs &a, Lane<GeneralMode
     }
 }
 
+// ------------------------------------------------------- tail compaction
+// Once the work queue has drained, lanes whose trajectories end stay idle
+// until every lane of their warp is done, and an issue-bound SM spends the
+// same issue slots on a warp with one busy lane as on a full one.  So a warp
+// whose unfinished trajectories fit into the idle lanes of the other warps of
+// its block hands them over through shared memory and leaves the work loop;
+// the block's remaining trajectories then run on fewer, fuller warps.
+// Between two step pairs a trajectory's whole state is (x, t, n, k, status,
+// item): everything else a lane holds is a function of the item (constants,
+// trajectory id, next sample time; random numbers are keyed by (id, n)), so
+// a move is exact and results do not depend on it.
+//
+// Protocol (one lock per block, taken by lane 0 of a warp; every wait on it
+// is bounded):
+//  * `live` has bit w set while warp w is in the loop.  A warp gives its
+//    trajectories away only while another warp is live and their idle lanes
+//    (as last reported in `act`) can take them; it then clears its bit.
+//  * A live warp leaves with no work only when the pool is empty (checked
+//    under the lock).  Hence whenever the pool holds records some live warp
+//    remains, and it takes them into idle lanes at its next refill check.
+//  * Each warp leaves once, so a trajectory moves at most warps - 1 times.
+constexpr int kPoolCap = 96;              // records held at once
+constexpr int kPoolWarps = 8;             // warps per block (blockDim <= 256)
+constexpr int kPoolLockSpins = 1 << 22;   // bound on the lock wait (under a second)
+
+template <class Model, int PREC>
+struct TailPool {
+    using P = typename ModeTraits<PREC>::P;
+    int lock;
+    int count;                  // records held, in slots 0 .. count-1
+    unsigned live;              // bit w: warp w still in the work loop
+    int act[kPoolWarps];        // busy lanes of warp w at its last check
+    int64_t item[kPoolCap];
+    int64_t n[kPoolCap];
+    P t[kPoolCap];
+    int k[kPoolCap];
+    uint32_t status[kPoolCap];
+    int x[Model::N][kPoolCap];
+};
+
+template <class Model, int PREC>
+__device__ __forceinline__ void pool_init(TailPool<Model, PREC> *p)
+{
+    if (threadIdx.x == 0) {
+        const int nw = (int)((blockDim.x + 31u) >> 5);
+        p->lock = 0;
+        p->count = 0;
+        p->live = (1u << nw) - 1u;
+        for (int w = 0; w < kPoolWarps; ++w) p->act[w] = 32;
+    }
+}
+
+__device__ __forceinline__ bool pool_acquire(int *lock)
+{
+    for (int i = 0; i < kPoolLockSpins; ++i) {
+        if (atomicCAS(lock, 0, 1) == 0) {
+            __threadfence_block();
+            return true;
+        }
+        __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void pool_release(int *lock)
+{
+    __threadfence_block();
+    atomicExch(lock, 0);
+}
+
+// Lane 0's decision at a pool visit (kept out of line: it runs only after the
+// queue has drained).  Returns (timeout << 31) | (op << 24) | (base << 12) | num.
+static __device__ __noinline__ unsigned pool_decide(int *lock, int *count_p, unsigned *live_p, int *act, int w, int nb,
+                                             unsigned long long *stats)
+{
+    volatile int *vcount = count_p;
+    volatile unsigned *vlive = live_p;
+    volatile int *vact = act;
+    int cnt = *vcount;
+    unsigned live = *vlive;
+    int room = -cnt;
+    for (int v = 0; v < kPoolWarps; ++v)
+        if (v != w && ((live >> v) & 1u)) room += 32 - vact[v];
+    const bool maybe = nb == 0 || (cnt > 0 && nb < 32) || (nb <= room && cnt + nb <= kPoolCap);
+    vact[w] = nb;
+    if (!maybe) return 0u;
+    if (!pool_acquire(lock)) {
+        atomicAdd(&stats[1], 1ull);
+        return 1u << 31;
+    }
+    cnt = *vcount;
+    live = *vlive;
+    room = -cnt;
+    for (int v = 0; v < kPoolWarps; ++v)
+        if (v != w && ((live >> v) & 1u)) room += 32 - vact[v];
+    unsigned op = 0, base = 0, num = 0;
+    if (cnt > 0 && nb < 32) {
+        op = 1;
+        num = (unsigned)min(cnt, 32 - nb);
+        base = (unsigned)cnt - num;
+        *vcount = (int)base;
+        vact[w] = nb + (int)num;
+    } else if (nb == 0) {
+        op = 3;
+        *vlive = live & ~(1u << w);
+    } else if (nb <= room && cnt + nb <= kPoolCap && (live & ~(1u << w)) != 0u) {
+        op = 2;
+        num = (unsigned)nb;
+        base = (unsigned)cnt;
+        *vcount = cnt + nb;
+        *vlive = live & ~(1u << w);
+    }
+    if (op == 0) pool_release(lock);
+    return (op << 24) | (base << 12) | num;
+}
+
+// One visit of a warp to its block's pool at a refill check (whole warp).
+// Takes records into idle lanes, or gives the warp's trajectories away.
+// Returns true when the warp leaves the work loop.
+template <class Model, int PREC>
+__device__ __forceinline__ bool pool_visit(const RunArgs &a, TailPool<Model, PREC> *p, Lane<Model, PREC> &L,
+                                           const typename ModeTraits<PREC>::P *smp)
+{
+    using P = typename ModeTraits<PREC>::P;
+    const unsigned lane = threadIdx.x & 31u;
+    const int w = (int)(threadIdx.x >> 5);
+    const unsigned busy = __ballot_sync(0xFFFFFFFFu, L.active);
+    const int nb = __popc(busy);
+    // 0 nothing, 1 take records, 2 give trajectories away, 3 leave (idle, pool empty)
+    int op = 0, base = 0, num = 0, ok = 1;
+    if (lane == 0) {
+        const unsigned r = pool_decide(&p->lock, &p->count, &p->live, p->act, w, nb, a.tail_stats);
+        ok = (int)(r >> 31) ^ 1;
+        op = (int)((r >> 24) & 0x7Fu);
+        base = (int)((r >> 12) & 0xFFFu);
+        num = (int)(r & 0xFFFu);
+    }
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    if (!ok) return nb == 0;   // lock wait gave up (counted): leave only if idle
+    op = __shfl_sync(0xFFFFFFFFu, op, 0);
+    if (op == 0) return false;
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    num = __shfl_sync(0xFFFFFFFFu, num, 0);
+    __syncwarp();
+    __threadfence_block();   // lane 0 holds the lock: the records are ours to read or write
+    const unsigned below = (1u << lane) - 1u;
+    if (op == 1 && !L.active) {
+        const int r = __popc(~busy & below);
+        if (r < num) {
+            const int s = base + r;
+            init_lane<Model, PREC>(a, L, p->item[s], smp);
+            L.n = p->n[s];
+            L.t = p->t[s];
+            L.k = p->k[s];
+            L.status = p->status[s];
+            unroll<Model::N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                L.x[i] = p->x[i][s];
+            });
+            L.s_next = L.k < a.K ? smp[L.k] : P(__int_as_float(0x7F800000));
+        }
+    } else if (op == 2 && L.active) {
+        const int s = base + __popc(busy & below);
+        p->item[s] = L.item;
+        p->n[s] = L.n;
+        p->t[s] = L.t;
+        p->k[s] = L.k;
+        p->status[s] = L.status;
+        unroll<Model::N>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            p->x[i][s] = L.x[i];
+        });
+        L.active = false;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        pool_release(&p->lock);
+        if (op == 2) atomicAdd(&a.tail_stats[0], (unsigned long long)num);
+    }
+    return op >= 2;
+}
+
 // ---------------------------------------------------------- the work loop
 // Persistent loop of one warp over one work queue: lanes that are idle take
 // the next items (one atomicAdd per warp), then every lane runs `slice_pairs`
 // pairs of steps (one Philox block of stream 0 per pair) before the next
-// refill check.  Returns once the queue is drained and every lane is idle,
-// so the caller may move the whole warp to another queue.
+// refill check.  With a pool (single-queue kernel), warps of a block hand
+// trajectories to each other once the queue has drained (tail compaction,
+// above).  Returns once the warp has no more work, so the caller may move the
+// whole warp to another queue.
 template <class Model, int PREC, int SR>
 __device__ __forceinline__ void run_queue(const RunArgs &a, const typename ModeTraits<PREC>::P *smp,
-                                          typename ModeTraits<PREC>::P t_end)
+                                          typename ModeTraits<PREC>::P t_end,
+                                          TailPool<Model, PREC> *pool = nullptr)
 {
     const unsigned lane = threadIdx.x & 31u;
     Lane<Model, PREC> L;
@@ -896,6 +1082,10 @@ __device__ __forceinline__ void run_queue(const RunArgs &a, const typename ModeT
                 if (item < (unsigned long long)a.n_work) init_lane<Model, PREC>(a, L, (int64_t)item, smp);
                 else drained = true;
             }
+        }
+        // the pool's count may change between lanes' reads: decide by ballot, warp-uniformly
+        if (pool && __any_sync(0xFFFFFFFFu, drained || *(volatile int *)&pool->count > 0)) {
+            if (pool_visit<Model, PREC>(a, pool, L, smp)) break;
         }
         if (__ballot_sync(0xFFFFFFFFu, L.active) == 0u) break;
         for (int s = 0; s < slice; ++s) {
@@ -928,8 +1118,10 @@ __global__ void __launch_bounds__(256, SSA_MIN_BLOCKS) ssa_kernel(const __grid_c
 {
     using P = typename ModeTraits<PREC>::P;
     __shared__ P smp[kMaxK];
-    load_samples<PREC>(a.samples, a.K, smp);
-    run_queue<Model, PREC, SR>(a, smp, to_time<PREC>(a.t_end));
+    __shared__ TailPool<Model, PREC> pool;
+    if (a.tail_stats) pool_init(&pool);
+    load_samples<PREC>(a.samples, a.K, smp);   // ends with __syncthreads
+    run_queue<Model, PREC, SR>(a, smp, to_time<PREC>(a.t_end), a.tail_stats ? &pool : nullptr);
 }
 
 // Several groups (heterogeneous structures and parameter sweeps), one queue

@@ -35,6 +35,8 @@ SIGNATURES = {
     "ssa_rdme_run": (_I, [_P, _I, _I, _I, _P, _I64, _U64, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, _P, _P, _P, _P,
                           _P]),
     "ssa_set_launch_config": (_I, [_I, _I, _I]),
+    "ssa_set_tail_compaction": (_I, [_I]),
+    "ssa_tail_stats": (_I, [ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "ssa_batch_create": (_I, [_I, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, ctypes.POINTER(_P)]),
     "ssa_batch_launch": (_I, [_P, _P]),
     "ssa_batch_autotune": (_I, [_P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -139,10 +141,23 @@ class Model:
             pass
 
 
-def set_launch_config(threads_per_block=128, blocks_per_sm=0, slice_pairs=16):
+def set_launch_config(threads_per_block=0, blocks_per_sm=0, slice_pairs=0):
     """Launch shape for later runs (speed only; results do not depend on it).
-    The defaults are the library's own starting shape."""
+    With no arguments, back to the library's defaults."""
     _check(lib().ssa_set_launch_config(int(threads_per_block), int(blocks_per_sm), int(slice_pairs)))
+
+
+def set_tail_compaction(enabled=True):
+    """Tail compaction of the direct-method kernel (speed only)."""
+    _check(lib().ssa_set_tail_compaction(1 if enabled else 0))
+
+
+def tail_stats():
+    """(trajectories moved between warps, lock waits given up) so far on the
+    current device; synchronises it."""
+    moved, timeouts = _I64(0), _I64(0)
+    _check(lib().ssa_tail_stats(ctypes.byref(moved), ctypes.byref(timeouts)))
+    return int(moved.value), int(timeouts.value)
 
 
 def _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision, rounding, normalise, seed,

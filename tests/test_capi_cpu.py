@@ -116,6 +116,13 @@ def test_launch_config_validation(ssa):
     ssa.set_launch_config()
 
 
+def test_tail_compaction_switch_validation(ssa):
+    assert ssa.lib().ssa_set_tail_compaction(2) == ssa.SSA_EINVAL
+    assert ssa.lib().ssa_set_tail_compaction(-1) == ssa.SSA_EINVAL
+    ssa.set_tail_compaction(False)
+    ssa.set_tail_compaction(True)
+
+
 def test_batch_create_rejects_before_allocating(ssa):
     """Group validation happens on the host before any device allocation."""
     m = ssa.Model.from_dict(P.telegraph())

@@ -141,7 +141,7 @@ def test_results_independent_of_launch_shape(ssa):
     tel = P.telegraph(0.3, 0.2, 10.0, 1.0)
     base = None
     try:
-        for block, per_sm, slice_pairs in [(128, 0, 1), (128, 0, 16), (32, 1, 3), (256, 2, 16), (64, 0, 2)]:
+        for block, per_sm, slice_pairs in [(128, 0, 1), (128, 0, 16), (256, 0, 32), (32, 1, 3), (256, 2, 16), (64, 0, 2)]:
             ssa.set_launch_config(block, per_sm, slice_pairs)
             g, _ = gpu_run(ssa, tel, P.TELEGRAPH_X0, 700, 20.0, P.even_samples(20.0, 5), "uniform_f16", "sr",
                            False, 8, 10**6)

@@ -1,0 +1,204 @@
+"""Tail compaction of the direct-method kernel: after the work queue drains,
+warps of a block hand unfinished trajectories to each other.  A trajectory's
+state moves whole, so every result must stay bit-identical to the oracle and
+to a run without compaction; the device counters must show that trajectories
+did move and that no lock wait gave up."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_00479_gb300 import presets as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ssa():
+    from paper_2605_00479_gb300 import build, ssa as mod
+    build.build()
+    assert torch.cuda.is_available()
+    mod.lib()
+    return mod
+
+
+def general_network():
+    """Matches no compiled structure: runs on the general kernel (8-species
+    records in the pool)."""
+    return {
+        "order": np.array([[1, 0, 1], [2, 0, 0], [0, 1, 0], [0, 3, 0], [0, 0, 0], [1, 0, 0]], np.int32),
+        "stoich": np.array([[1, 0, -1], [-2, 1, 0], [1, -1, 0], [0, -3, 0], [0, 1, 0], [-1, 0, 0]], np.int32),
+        "rate": np.array([0.02, 0.01, 0.5, 0.001, 2.0, 0.1]),
+        "law": np.zeros(6, np.int32),
+        "constant": np.array([0, 0, 1], np.uint8),
+    }
+
+
+CASES = {
+    # name: (model, x0, n_traj, t_end, samples, normalise, max_events, precision, rounding)
+    "schlogl_uniform_f16_sr": (P.schlogl(), None, 20000, 2.0, P.even_samples(2.0, 5), True, 10**6, "uniform_f16",
+                               "sr"),
+    "schlogl_uniform_bf16_rn_capped": (P.schlogl(), None, 9000, 2.0, P.even_samples(2.0, 5), True, 3000,
+                                       "uniform_bf16", "rn"),
+    "telegraph_mixed_bf16_sr": (P.telegraph(0.5, 0.5, 20.0, 1.0), P.TELEGRAPH_X0, 12000, 20.0,
+                                P.even_samples(20.0, 7), False, 10**6, "mixed_bf16", "sr"),
+    "repressilator_fp32": (P.repressilator(), P.REPRESSILATOR_X0, 3000, 2.0, P.even_samples(2.0, 3), False, 10**6,
+                           "fp32", "rn"),
+    "general_network_uniform_f16_sra": (general_network(), [10, 5, 50], 8000, 20.0, P.even_samples(20.0, 5), True,
+                                        10**6, "uniform_f16", "sra"),
+    "dimer_fp64": (P.dimer(), P.dimer_x0(300), 4000, 5.0, P.even_samples(5.0, 4), False, 10**6, "fp64", "rn"),
+}
+
+
+_ORACLE = {}
+
+
+def oracle_case(name, seed, state_bytes=4):
+    """The oracle's ensemble for a case (computed once per module)."""
+    key = (name, seed, state_bytes)
+    if key not in _ORACLE:
+        md, x0, n, t_end, samples, norm, cap, prec, rnd = CASES[name]
+        x0 = P.schlogl_x0(md) if x0 is None else x0
+        _ORACLE[key] = oracle.run_parallel(md, x0, n, t_end, samples, precision=prec, rounding=rnd, normalise=norm,
+                                           seed=seed, max_events=cap, state_bytes=state_bytes)
+    return _ORACLE[key]
+
+
+def gpu_run(ssa, md, x0, n, t_end, samples, prec, rnd, norm, seed, cap, state_bytes=4):
+    m = ssa.Model.from_dict(md)
+    r = ssa.ensemble_run(m, n, x0, t_end, samples, prec, rnd, norm, seed, cap, state_bytes)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in r.items()}
+
+
+def assert_same(g, o):
+    np.testing.assert_array_equal(g["snapshots"], o["snapshots"])
+    np.testing.assert_array_equal(g["status"].view(np.uint32), np.asarray(o["status"]).view(np.uint32))
+    np.testing.assert_array_equal(g["n_events"], o["n_events"])
+    gt, ot = g["t_final"], o["t_final"]
+    both_nan = np.isnan(gt) & np.isnan(ot)
+    np.testing.assert_array_equal(gt.view(np.uint64)[~both_nan], ot.view(np.uint64)[~both_nan])
+
+
+@pytest.mark.parametrize("block,slice_pairs", [(256, 1), (128, 16), (64, 3)])
+@pytest.mark.parametrize("name", list(CASES))
+def test_compaction_matches_oracle(ssa, name, block, slice_pairs):
+    """One block per SM, so the queue drains at the first refill and lanes
+    retire unevenly: trajectories must move, and results equal the oracle."""
+    md, x0, n, t_end, samples, norm, cap, prec, rnd = CASES[name]
+    if x0 is None:
+        x0 = P.schlogl_x0(md)
+    sb = 2 if block == 64 else 4        # int16 snapshots (reservoirs clamp and flag, on both sides)
+    o = oracle_case(name, 41, sb)
+    try:
+        ssa.set_launch_config(block, 1, slice_pairs)
+        ssa.set_tail_compaction(True)
+        moved0, to0 = ssa.tail_stats()
+        g = gpu_run(ssa, md, x0, n, t_end, samples, prec, rnd, norm, 41, cap, state_bytes=sb)
+        moved1, to1 = ssa.tail_stats()
+    finally:
+        ssa.set_launch_config()
+    assert to1 == to0 == 0
+    assert moved1 >= moved0     # whether anything moves depends on the case (equal lengths: nothing)
+    assert_same(g, o)
+
+
+@pytest.mark.parametrize("name", ["schlogl_uniform_f16_sr", "telegraph_mixed_bf16_sr",
+                                  "general_network_uniform_f16_sra"])
+def test_compaction_moves_trajectories(ssa, name):
+    """Cases whose trajectory lengths spread widely: with one 256-thread block
+    per SM trajectories do move, and the results still equal the oracle."""
+    md, x0, n, t_end, samples, norm, cap, prec, rnd = CASES[name]
+    x0 = P.schlogl_x0(md) if x0 is None else x0
+    o = oracle_case(name, 41)
+    try:
+        ssa.set_launch_config(256, 1, 1)
+        moved0, to0 = ssa.tail_stats()
+        g = gpu_run(ssa, md, x0, n, t_end, samples, prec, rnd, norm, 41, cap)
+        moved1, to1 = ssa.tail_stats()
+    finally:
+        ssa.set_launch_config()
+    assert to1 == to0 == 0
+    assert moved1 > moved0
+    assert_same(g, o)
+
+
+def test_compaction_off_moves_nothing(ssa):
+    md, x0, n, t_end, samples, norm, cap, prec, rnd = CASES["telegraph_mixed_bf16_sr"]
+    o = oracle_case("telegraph_mixed_bf16_sr", 5)
+    try:
+        ssa.set_launch_config(256, 1, 1)
+        ssa.set_tail_compaction(False)
+        moved0, _ = ssa.tail_stats()
+        g = gpu_run(ssa, md, x0, n, t_end, samples, prec, rnd, norm, 5, cap)
+        moved1, to1 = ssa.tail_stats()
+    finally:
+        ssa.set_tail_compaction(True)
+        ssa.set_launch_config()
+    assert moved1 == moved0 and to1 == 0
+    assert_same(g, o)
+
+
+@pytest.mark.parametrize("prec,rnd", [("uniform_f16", "rn"), ("mixed_f16", "rn"), ("uniform_bf16", "sr")])
+def test_full_size_schlogl_on_off_identical(ssa, prec, rnd):
+    """The benchmark's workload in its default launch shape: the whole 10^6
+    ensemble is identical with and without compaction (each side is checked
+    against the oracle on sampled ids elsewhere), and compaction moved
+    trajectories."""
+    md = P.schlogl()
+    x0 = P.schlogl_x0(md)
+    samples = P.even_samples(10.0, 50)
+    moved0, to0 = ssa.tail_stats()
+    on = gpu_run(ssa, md, x0, 10**6, 10.0, samples, prec, rnd, True, 77, 200000)
+    moved1, to1 = ssa.tail_stats()
+    try:
+        ssa.set_tail_compaction(False)
+        off = gpu_run(ssa, md, x0, 10**6, 10.0, samples, prec, rnd, True, 77, 200000)
+    finally:
+        ssa.set_tail_compaction(True)
+    assert to1 == to0 == 0
+    assert moved1 > moved0
+    assert_same(on, off)
+    for r in [0, 123457, 999999]:
+        o = oracle.run(md, x0, 1, 10.0, samples, prec, rnd, True, 77, 200000, g0=r)
+        np.testing.assert_array_equal(on["snapshots"][:, :, r], o["snapshots"][:, :, 0])
+        assert on["n_events"][r] == o["n_events"][0]
+
+
+def test_noalloc_sweep_with_compaction(ssa):
+    """The allocation-free sweep entry point compacts too; every set equals
+    the oracle run with that set's rate constants."""
+    import ctypes
+    tel = P.telegraph(0.3, 0.3, 20.0, 1.0)
+    rates = np.ascontiguousarray(P.telegraph_sweep(3, seed=17))
+    S, per = rates.shape[0], 2000
+    x0 = np.ascontiguousarray(np.tile(P.TELEGRAPH_X0, (S, 1)), dtype=np.int32)
+    samples = np.ascontiguousarray(P.even_samples(10.0, 4), dtype=np.float64)
+    m = ssa.Model.from_dict(tel)
+    n = S * per
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = torch.full((4, m.N, n), -7, dtype=torch.int32, device=dev)
+    st = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    ev = torch.full((n,), -7, dtype=torch.int64, device=dev)
+    tf = torch.full((n,), -7.0, dtype=torch.float64, device=dev)
+    vp = ctypes.c_void_p
+    try:
+        ssa.set_launch_config(256, 1, 1)
+        moved0, _ = ssa.tail_stats()
+        rc = ssa.lib().ssa_sweep_run_noalloc(
+            m.handle, S, per, rates.ctypes.data_as(vp), None, x0.ctypes.data_as(vp), 0, 10.0, 4,
+            samples.ctypes.data_as(vp), ssa.PRECISION["mixed_f16"], ssa.ROUNDING["rn"], 0, 8, 10**6, 4,
+            vp(out.data_ptr()), vp(st.data_ptr()), vp(ev.data_ptr()), vp(tf.data_ptr()),
+            vp(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0, ssa.lib().ssa_last_error()
+        moved1, to1 = ssa.tail_stats()
+    finally:
+        ssa.set_launch_config()
+    assert to1 == 0 and moved1 > moved0
+    snaps, evs = out.cpu().numpy(), ev.cpu().numpy()
+    for q in range(S):
+        mq = dict(tel)
+        mq["rate"] = rates[q]
+        o = oracle.run(mq, P.TELEGRAPH_X0, per, 10.0, samples, "mixed_f16", "rn", False, 8, 10**6, g0=q * per)
+        np.testing.assert_array_equal(snaps[:, :, q * per:(q + 1) * per], o["snapshots"])
+        np.testing.assert_array_equal(evs[q * per:(q + 1) * per], o["n_events"])

@@ -150,14 +150,21 @@ int ssa_ensemble_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offse
                      int64_t *n_events, double *t_final, void *stream);
 
 /*
- * ssa_ensemble_run_host -- ssa_ensemble_run with HOST output buffers.  The
- * call allocates device buffers, launches, copies the results back and
+ * ssa_ensemble_run_host -- ssa_ensemble_run with HOST output buffers;
  * synchronises the stream before returning.  out, traj_status, n_events and
  * t_final are host pointers with the layouts above (n_events, t_final may be
- * NULL).  Page-locked host memory makes the copies faster.  The device
- * buffers come from a memory pool private to the library that keeps its
- * reservation between calls (the largest call's size, per device, until the
- * process exits), so repeated calls do not remap device memory.
+ * NULL).
+ *  - If every given output is page-locked host memory that the current
+ *    device addresses under the same pointer (cudaHostAlloc, or
+ *    cudaHostRegister with mapping; unified addressing), the kernel writes
+ *    the results straight into it as the ensemble runs -- on Grace-Blackwell
+ *    over NVLink-C2C -- with no device buffers and no copy afterwards.
+ *  - Otherwise the call stages the results in device buffers and copies them
+ *    back after the kernel.  The device buffers come from a memory pool
+ *    private to the library that keeps its reservation between calls (the
+ *    largest call's size, per device, until the process exits), so repeated
+ *    calls do not remap device memory.
+ * Results are the same either way.
  */
 int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_offset,
                           const int32_t *x0, double t_end, int n_samples, const double *sample_times,

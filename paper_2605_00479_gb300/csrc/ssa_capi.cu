@@ -435,6 +435,21 @@ cudaError_t staging_pool(cudaMemPool_t *out)
     return cudaSuccess;
 }
 
+// Address under which this device reaches page-locked host memory `p`, or
+// null when `p` is not page-locked, not mapped for this device, or not
+// reachable under its own (unified) address.
+void *pinned_for_device(void *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || at.devicePointer != p) return nullptr;
+    return p;
+}
+
 }  // namespace
 
 extern "C" {
@@ -450,6 +465,17 @@ int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_
     if (n_traj > 0 && (!out || !traj_status)) return fail(SSA_EINVAL, "out and traj_status are required");
     if (n_traj == 0) return SSA_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // Page-locked outputs: the kernel writes the results straight into them
+    // while it runs (over NVLink-C2C on Grace-Blackwell), with no staging
+    // buffers and no copy after the kernel.
+    if (pinned_for_device(out) && pinned_for_device(traj_status) && (!n_events || pinned_for_device(n_events)) &&
+        (!t_final || pinned_for_device(t_final))) {
+        rc = launch_run(model, n_traj, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
+                        normalise, seed, max_events, state_bytes, out, traj_status, n_events, t_final, s);
+        const cudaError_t es = cudaStreamSynchronize(s);
+        if (rc == SSA_OK && es != cudaSuccess) rc = cuda_fail(es, "cudaStreamSynchronize");
+        return rc;
+    }
     const size_t out_bytes = (size_t)n_samples * (size_t)model->N * (size_t)n_traj * (size_t)state_bytes;
     const size_t st_bytes = (size_t)n_traj * sizeof(uint32_t);
     const size_t ev_bytes = n_events ? (size_t)n_traj * sizeof(int64_t) : 0;

@@ -177,6 +177,38 @@ def test_large_host_entry_point_matches_device(ssa, state_bytes):
     assert_same({**h, "status": h["status"].view(np.int32)}, {**g, "status": g["status"].view(np.uint32)})
 
 
+@pytest.mark.parametrize("pinned", ["all", "all_but_status", "no_optional"])
+def test_host_entry_point_page_locked_outputs(ssa, pinned):
+    """Page-locked outputs take the direct-write path (the kernel writes into
+    host memory); a pageable buffer among them sends the call through device
+    staging.  Results equal the device entry point either way."""
+    tel = P.telegraph(0.5, 0.5, 20.0, 1.0)
+    m = ssa.Model.from_dict(tel)
+    n, off = 200003, 777
+    samples = P.even_samples(5.0, 6)
+    K = len(samples)
+    out = torch.full((K, m.N, n), -5, dtype=torch.int32).pin_memory()
+    st = torch.full((n,), -5, dtype=torch.int32)
+    st = st.pin_memory() if pinned != "all_but_status" else st
+    ev = torch.full((n,), -5, dtype=torch.int64).pin_memory() if pinned != "no_optional" else None
+    tf = torch.full((n,), -5.0, dtype=torch.float64).pin_memory() if pinned != "no_optional" else None
+    import ctypes
+    vp = ctypes.c_void_p
+    x0 = np.ascontiguousarray(P.TELEGRAPH_X0, dtype=np.int32)
+    smp = np.ascontiguousarray(samples, dtype=np.float64)
+    rc = ssa.lib().ssa_ensemble_run_host(
+        m.handle, n, off, x0.ctypes.data_as(vp), 5.0, K, smp.ctypes.data_as(vp), ssa.PRECISION["mixed_bf16"],
+        ssa.ROUNDING["sr"], 0, 13, 10**5, 4, vp(out.data_ptr()), vp(st.data_ptr()),
+        None if ev is None else vp(ev.data_ptr()), None if tf is None else vp(tf.data_ptr()), None)
+    assert rc == 0, ssa.lib().ssa_last_error()
+    g, _ = gpu_run(ssa, tel, P.TELEGRAPH_X0, n, 5.0, samples, "mixed_bf16", "sr", False, 13, 10**5, traj_offset=off)
+    np.testing.assert_array_equal(out.numpy(), g["snapshots"])
+    np.testing.assert_array_equal(st.numpy(), g["status"])
+    if ev is not None:
+        np.testing.assert_array_equal(ev.numpy(), g["n_events"])
+        np.testing.assert_array_equal(tf.numpy().view(np.uint64), g["t_final"].view(np.uint64))
+
+
 BENCH_MODES = [("mixed_f16", "rn"), ("mixed_bf16", "rn"), ("uniform_f16", "rn"), ("uniform_f16", "sr"),
                ("uniform_bf16", "sr"), ("uniform_f16", "sra"), ("mixed_f16", "sr")]
 

@@ -152,6 +152,7 @@ struct RdmeView {
     P *node;               // &node_columns[lane]; node q at (q * bd)
     uint32_t *epoch;       // &epoch_columns[lane] or null
     int bd, ns;
+    unsigned dmask;        // bit i: species i hops (D_i > 0), so the hot path makes no binary64 compare
     __device__ __forceinline__ int32_t &at(int v, int s) const { return x[(v * ns + s) * bd]; }
     __device__ __forceinline__ P &Node(int q) const { return node[q * bd]; }
 };
@@ -273,7 +274,7 @@ __device__ __forceinline__ typename ModeTraits<PREC>::P rdme_voxel(const RdmeArg
         unroll<N>([&](auto I) {
             constexpr int i = decltype(I)::value;
             hv[i] = P(0);
-            if (nnb > 0 && A.D[i] > 0.0) {
+            if (nnb > 0 && ((W.dmask >> i) & 1u)) {
                 const int xi = rdme_get<Model, i>(W, v);
                 if (xi < 1) {
                     op += 2;
@@ -288,7 +289,7 @@ __device__ __forceinline__ typename ModeTraits<PREC>::P rdme_voxel(const RdmeArg
         if (nnb > 0) {
             unroll<N>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                if (A.D[i] > 0.0)
+                if ((W.dmask >> i) & 1u)
                     for (int d = 0; d < nnb; ++d) cs.add(hv[i]);
             });
         }
@@ -327,7 +328,7 @@ __device__ __forceinline__ typename ModeTraits<PREC>::P rdme_voxel(const RdmeArg
 #pragma unroll 1
         for (int i = 0; i < N; ++i) {
             hv[i] = P(0);
-            if (nnb == 0 || !(A.D[i] > 0.0)) continue;
+            if (nnb == 0 || !((W.dmask >> i) & 1u)) continue;
             const int xi = W.at(v, i);
             if (xi < 1) {
                 op += 2;
@@ -342,7 +343,7 @@ __device__ __forceinline__ typename ModeTraits<PREC>::P rdme_voxel(const RdmeArg
         if (nnb > 0) {
 #pragma unroll 1
             for (int i = 0; i < N; ++i) {
-                if (!(A.D[i] > 0.0)) continue;
+                if (!((W.dmask >> i) & 1u)) continue;
                 for (int d = 0; d < nnb; ++d) cs.add(hv[i]);
             }
         }
@@ -351,13 +352,15 @@ __device__ __forceinline__ typename ModeTraits<PREC>::P rdme_voxel(const RdmeArg
     return cs.S;
 }
 
+// Tree node q at epoch e from its children's values (left + right).
 template <int PREC, int SR>
-__device__ __forceinline__ typename ModeTraits<PREC>::P rdme_node(const RdmeArgs &A, const RdmeView<PREC> &W, int q,
-                                                                  uint32_t e, uint32_t traj)
+__device__ __forceinline__ typename ModeTraits<PREC>::P rdme_sum(const RdmeArgs &A, typename ModeTraits<PREC>::P lf,
+                                                                 typename ModeTraits<PREC>::P rt, int q, uint32_t e,
+                                                                 uint32_t traj)
 {
     using Tr = ModeTraits<PREC>;
     using P = typename Tr::P;
-    const P s = W.Node(2 * q) + W.Node(2 * q + 1);
+    const P s = lf + rt;
     if constexpr (Tr::kUniform) {
         if constexpr (SR != 0) {
             const uint4 b = philox4x32_10(make_uint4(0u, e, traj, 0x40000000u | (uint32_t)q), A.a.key0, A.a.key1);
@@ -368,6 +371,13 @@ __device__ __forceinline__ typename ModeTraits<PREC>::P rdme_node(const RdmeArgs
     } else {
         return s;
     }
+}
+
+template <int PREC, int SR>
+__device__ __forceinline__ typename ModeTraits<PREC>::P rdme_node(const RdmeArgs &A, const RdmeView<PREC> &W, int q,
+                                                                  uint32_t e, uint32_t traj)
+{
+    return rdme_sum<PREC, SR>(A, W.Node(2 * q), W.Node(2 * q + 1), q, e, traj);
 }
 
 __device__ __forceinline__ void rdme_put(const RunArgs &a, int64_t idx, int val, uint32_t &status)
@@ -495,7 +505,7 @@ __device__ __forceinline__ int rdme_apply(const RdmeArgs &A, const RdmeView<PREC
     const int nnb = __popc((unsigned)nb);
 #pragma unroll 1
     for (int i = 0; i < a.N && species < 0; ++i) {
-        if (!(A.D[i] > 0.0)) continue;
+        if (!((W.dmask >> i) & 1u)) continue;
         if (idx < nnb) {
             species = i;
             int seen = 0;
@@ -596,21 +606,43 @@ __device__ __forceinline__ void rdme_event(const RdmeArgs &A, const RdmeView<PRE
     }
     if (t_new > t_end) { rdme_finish<Model, PREC>(A, W, L); return; }
 
-    // voxel by descent of the sum tree
+    // voxel by descent of the sum tree, two levels per round of shared-memory
+    // reads: a node's children and all four grandchildren are read together,
+    // and the second level takes its pair from the grandchildren
     int q = 1, level = 0;
     P r = target;
 #pragma unroll 1
     while (q < T) {
         const P lf = W.Node(2 * q), rt = W.Node(2 * q + 1);
+        const bool deeper = 2 * q < T;   // children internal (then 4q + 3 <= 2T - 1)
+        P g0 = P(0), g1 = P(0), g2 = P(0), g3 = P(0);
+        if (deeper) {
+            g0 = W.Node(4 * q);
+            g1 = W.Node(4 * q + 1);
+            g2 = W.Node(4 * q + 2);
+            g3 = W.Node(4 * q + 3);
+        }
+        bool right = false;
         if (lf > r) {
-            q = 2 * q;
+            right = false;
         } else if (rt > P(0)) {
             if constexpr (Tr::kUniform) r = R.rnd(r - lf, 5 + level);
             else r = r - lf;
-            q = 2 * q + 1;
-        } else {
-            q = 2 * q;
+            right = true;
         }
+        q = 2 * q + (right ? 1 : 0);
+        level += 1;
+        if (!deeper) break;
+        const P lf2 = right ? g2 : g0, rt2 = right ? g3 : g1;
+        right = false;
+        if (lf2 > r) {
+            right = false;
+        } else if (rt2 > P(0)) {
+            if constexpr (Tr::kUniform) r = R.rnd(r - lf2, 5 + level);
+            else r = r - lf2;
+            right = true;
+        }
+        q = 2 * q + (right ? 1 : 0);
         level += 1;
     }
     const int v = q - T;
@@ -631,27 +663,62 @@ __device__ __forceinline__ void rdme_event(const RdmeArgs &A, const RdmeView<PRE
         rdme_finish<Model, PREC>(A, W, L);
         return;
     }
-    // recompute the changed voxels and their ancestors at epoch n + 1
+    // recompute the changed voxels and their ancestors at epoch n + 1.  The
+    // new values climb the tree in registers; only the siblings are read from
+    // shared memory, all of them before the first sum.  A sibling on the other
+    // path is never read: there the two paths meet and both values are at hand.
+    constexpr int kMaxDepth = 10;   // T <= kMaxVoxels = 1024
+    const int depth = A.depth;
+    const int la = T + v, lb = w >= 0 ? T + w : 0;
+    P sa[kMaxDepth], sb[kMaxDepth];
+#pragma unroll
+    for (int l = 0; l < kMaxDepth; ++l) {
+        sa[l] = P(0);
+        sb[l] = P(0);
+        if (l < depth) {
+            sa[l] = W.Node((la >> l) ^ 1);
+            if (lb) sb[l] = W.Node((lb >> l) ^ 1);
+        }
+    }
     const uint32_t e = (uint32_t)L.n;
-    W.Node(T + v) = rdme_voxel<Model, PREC, SR>(A, W, v, e, L.traj, P(0), nullptr);
+    P va = rdme_voxel<Model, PREC, SR>(A, W, v, e, L.traj, P(0), nullptr);
+    W.Node(la) = va;
     if (W.epoch) W.epoch[v * W.bd] = e;
+    P vb = P(0);
     if (w >= 0) {
-        W.Node(T + w) = rdme_voxel<Model, PREC, SR>(A, W, w, e, L.traj, P(0), nullptr);
+        vb = rdme_voxel<Model, PREC, SR>(A, W, w, e, L.traj, P(0), nullptr);
+        W.Node(lb) = vb;
         if (W.epoch) W.epoch[w * W.bd] = e;
     }
-    int qa = (T + v) >> 1, qb = w >= 0 ? (T + w) >> 1 : 0;
-#pragma unroll 1
-    while (qa >= 1) {
-        if (qb == qa) qb = 0;
-        W.Node(qa) = rdme_node<PREC, SR>(A, W, qa, e, L.traj);
-        if (qb) W.Node(qb) = rdme_node<PREC, SR>(A, W, qb, e, L.traj);
-        qa >>= 1;
-        qb >>= 1;
+    int qa = la, qb = lb;
+#pragma unroll
+    for (int l = 0; l < kMaxDepth; ++l) {
+        if (l >= depth) break;
+        const int pa = qa >> 1;
+        if (qb != 0 && (qb >> 1) == pa) {            // the paths meet at pa
+            const P lf = (qa & 1) ? vb : va, rt = (qa & 1) ? va : vb;
+            va = rdme_sum<PREC, SR>(A, lf, rt, pa, e, L.traj);
+            qb = 0;
+        } else {
+            const P lf = (qa & 1) ? sa[l] : va, rt = (qa & 1) ? va : sa[l];
+            va = rdme_sum<PREC, SR>(A, lf, rt, pa, e, L.traj);
+            if (qb != 0) {
+                const int pb = qb >> 1;
+                const P lfb = (qb & 1) ? sb[l] : vb, rtb = (qb & 1) ? vb : sb[l];
+                vb = rdme_sum<PREC, SR>(A, lfb, rtb, pb, e, L.traj);
+                W.Node(pb) = vb;
+                qb = pb;
+            }
+        }
+        W.Node(pa) = va;
+        qa = pa;
     }
 }
 
 // Persistent RDME kernel: lanes refill from the work queue; each loop
-// iteration runs one event.
+// iteration runs up to kRdmeSlice events per lane.
+constexpr int kRdmeSlice = 8;
+
 template <class Model, int PREC, int SR>
 __global__ void __launch_bounds__(256) rdme_kernel(const __grid_constant__ RdmeArgs A)
 {
@@ -703,6 +770,9 @@ __global__ void __launch_bounds__(256) rdme_kernel(const __grid_constant__ RdmeA
     W.epoch = kEpochs ? reinterpret_cast<uint32_t *>(rdme_smem + lay.epoch) + tid : nullptr;
     W.bd = bd;
     W.ns = A.n_stored;
+    W.dmask = 0u;
+    for (int i = 0; i < kMaxN; ++i)
+        if (i < a.N && A.D[i] > 0.0) W.dmask |= 1u << i;
     const P t_end = to_time<PREC>(a.t_end);
 
     const unsigned lane = threadIdx.x & 31u;
@@ -723,7 +793,11 @@ __global__ void __launch_bounds__(256) rdme_kernel(const __grid_constant__ RdmeA
             }
         }
         if (__ballot_sync(0xFFFFFFFFu, L.active) == 0u) break;
-        if (L.active) rdme_event<Model, PREC, SR>(A, W, L, t_end);
+        // several events between refill checks (a lane that finishes idles
+        // until the slice ends)
+#pragma unroll 1
+        for (int sl = 0; sl < kRdmeSlice; ++sl)
+            if (L.active) rdme_event<Model, PREC, SR>(A, W, L, t_end);
     }
 }
 

@@ -287,16 +287,28 @@ __device__ __noinline__ int64_t poisson_call(typename ModeTraits<PREC>::P lam, S
     else return poisson_f32(lam, s);
 }
 
-// One leap n = L.n of an active lane.
+// Smallest m >= 0 with fl(m * tau) > s in binary64.  Since fl(m * tau) does
+// not decrease with m, "s < fl((n + 1) * tau)" (snapshot s is written before
+// leap n) is "n + 1 >= m": the leap loop then needs no binary64 operation.
+__device__ inline int64_t first_leap_after(double s, double tau)
+{
+    const double g = floor(s / tau);
+    int64_t m = g < 0.0 ? 0 : (g > 4.0e18 ? (int64_t)4.0e18 : (int64_t)g);
+    for (int i = 0; i < 64 && !((double)m * tau > s); ++i) ++m;
+    for (int i = 0; i < 64 && m > 0 && (double)(m - 1) * tau > s; ++i) --m;
+    return m;
+}
+
+// One leap n = L.n of an active lane.  m_first[k]: first_leap_after(sample
+// k, tau); tau32: tau rounded to binary32.
 template <class Model, int PREC, int SR>
-__device__ __noinline__ void tau_leap(const RunArgs &a, Lane<Model, PREC> &L, const double *smp)
+__device__ __noinline__ void tau_leap(const RunArgs &a, Lane<Model, PREC> &L, const int64_t *m_first, float tau32)
 {
     using Tr = ModeTraits<PREC>;
     using P = typename Tr::P;
     constexpr bool kGeneral = std::is_same<Model, GeneralModel>::value;
     const int64_t n = L.n;
-    const double t_next = (double)(n + 1) * a.tau;
-    while (L.k < a.K && smp[L.k] < t_next) {
+    while (L.k < a.K && n + 1 >= m_first[L.k]) {
         store_state<Model>(a, L.k, L.item, L.x, L.status);
         L.k += 1;
     }
@@ -309,7 +321,6 @@ __device__ __noinline__ void tau_leap(const RunArgs &a, Lane<Model, PREC> &L, co
         R.bits.k1 = a.key1;
         R.bits.cur = -1;
     }
-    const float tau32 = (float)a.tau;
     float tau16 = tau32;
     if constexpr (Tr::k16) tau16 = rn16<Tr::kFmt>(tau32);
     const int lam_op = Model::total_chain_ops(a);   // SR slot of lambda_0 (uniform modes)
@@ -412,9 +423,10 @@ template <class Model, int PREC, int SR>
 __global__ void __launch_bounds__(256) tau_kernel(const __grid_constant__ RunArgs a)
 {
     using P = typename ModeTraits<PREC>::P;
-    __shared__ double smp[kMaxK];
-    for (int k = threadIdx.x; k < a.K; k += blockDim.x) smp[k] = a.samples[k];
+    __shared__ int64_t m_first[kMaxK];
+    for (int k = threadIdx.x; k < a.K; k += blockDim.x) m_first[k] = first_leap_after(a.samples[k], a.tau);
     __syncthreads();
+    const float tau32 = (float)a.tau;
     const unsigned lane = threadIdx.x & 31u;
     const P no_samples[1] = {P(0)};
     Lane<Model, PREC> L;
@@ -439,7 +451,7 @@ __global__ void __launch_bounds__(256) tau_kernel(const __grid_constant__ RunArg
             }
         }
         if (__ballot_sync(0xFFFFFFFFu, L.active) == 0u) break;
-        if (L.active) tau_leap<Model, PREC, SR>(a, L, smp);
+        if (L.active) tau_leap<Model, PREC, SR>(a, L, m_first, tau32);
     }
 }
 

@@ -13,7 +13,10 @@
  *  - Plain pointers and sizes only.  "host" pointers are read during the call
  *    and may be freed when it returns; "device" pointers are CUDA global
  *    memory owned by the caller and must stay valid until the work queued on
- *    the stream has finished.
+ *    the stream has finished.  A device output may also be page-locked host
+ *    memory that the device addresses under the same pointer (cudaHostAlloc,
+ *    unified addressing): the kernel then writes its results straight into
+ *    host memory (over NVLink-C2C on Grace-Blackwell).
  *  - Functions return SSA_OK (0) or a negative ssa_status.  Invalid arguments
  *    are rejected on the host before anything is launched (SSA_EINVAL); the
  *    message is available from ssa_last_error() on the calling thread.

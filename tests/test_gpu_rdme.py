@@ -147,3 +147,24 @@ def test_rdme_event_cap_and_overflow(ssa):
                         rounding="rn", seed=1, max_events=100)
     assert_same(g, o)
     assert np.all(o["status"] & 1)
+
+
+def test_rdme_outputs_in_page_locked_host_memory(ssa):
+    """Page-locked host buffers passed as the outputs: the kernel writes into
+    host memory directly; results equal the device-buffer run."""
+    model, dims, D, x0, _, t_end, samples, norm, cap = CASES["dimer_2d"]
+    m = ssa.Model.from_dict(model)
+    n = 3001
+    S = int(np.prod(dims))
+    K = len(samples)
+    host = {"out": torch.full((K, S, m.N, n), -9, dtype=torch.int32).pin_memory(),
+            "status": torch.full((n,), -9, dtype=torch.int32).pin_memory(),
+            "n_events": torch.full((n,), -9, dtype=torch.int64).pin_memory(),
+            "t_final": torch.full((n,), -9.0, dtype=torch.float64).pin_memory()}
+    ssa.rdme_run(m, dims, D, x0, n, t_end, samples, "mixed_f16", "sr", norm, 12, cap, **host)
+    torch.cuda.synchronize()
+    g = gpu_rdme(ssa, model, dims, D, x0, n, t_end, samples, "mixed_f16", "sr", norm, 12, cap)
+    np.testing.assert_array_equal(host["out"].numpy(), g["snapshots"])
+    np.testing.assert_array_equal(host["status"].numpy(), g["status"])
+    np.testing.assert_array_equal(host["n_events"].numpy(), g["n_events"])
+    np.testing.assert_array_equal(host["t_final"].numpy().view(np.uint64), g["t_final"].view(np.uint64))

@@ -147,3 +147,23 @@ def test_tau_single_leap_and_off_grid_end(ssa):
         o = oracle.tau_run(model, [5], 200, t_end, tau, samples, precision="uniform_f16", rounding="rn", seed=4)
         assert_same(g, o)
         assert np.all(o["t_final"] == np.ceil(t_end / tau) * tau)
+
+
+def test_tau_outputs_in_page_locked_host_memory(ssa):
+    """Page-locked host buffers passed as the outputs: the kernel writes into
+    host memory directly; results equal the device-buffer run."""
+    md = P.schlogl()
+    x0 = P.schlogl_x0(md)
+    m = ssa.Model.from_dict(md)
+    n, samples = 50001, P.even_samples(2.0, 5)
+    host = {"out": torch.full((5, m.N, n), -9, dtype=torch.int32).pin_memory(),
+            "status": torch.full((n,), -9, dtype=torch.int32).pin_memory(),
+            "n_events": torch.full((n,), -9, dtype=torch.int64).pin_memory(),
+            "t_final": torch.full((n,), -9.0, dtype=torch.float64).pin_memory()}
+    ssa.tau_run(m, n, x0, 2.0, 0.005, samples, "uniform_bf16", "sr", True, 21, traj_offset=99, **host)
+    torch.cuda.synchronize()
+    g = gpu_tau(ssa, md, x0, n, 2.0, 0.005, samples, "uniform_bf16", "sr", True, 21, traj_offset=99)
+    np.testing.assert_array_equal(host["out"].numpy(), g["snapshots"])
+    np.testing.assert_array_equal(host["status"].numpy(), g["status"])
+    np.testing.assert_array_equal(host["n_events"].numpy(), g["n_events"])
+    np.testing.assert_array_equal(host["t_final"].numpy().view(np.uint64), g["t_final"].view(np.uint64))

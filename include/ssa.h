@@ -261,9 +261,10 @@ int ssa_rdme_run(const ssa_model *model, int nx, int ny, int nz, const double *d
  *   slice_pairs        pairs of steps each lane runs between two checks for
  *                      finished lanes to refill, 1..64
  * threads_per_block = 0 restores the library's defaults (the other arguments
- * are then ignored): (256, 0, 32) for single-queue direct-method runs and
- * (128, 0, 16) for tau-leaping, RDME and batches, the fastest measured for
- * each.  Once a shape is set, every kind of run uses it.  Tau-leaping and
+ * are then ignored): for single-queue direct-method runs 32 step pairs per
+ * check and, per kernel, 256 threads per block unless that keeps fewer than
+ * 85% of the resident warps 128-thread blocks would (then 128); (128, 0, 16)
+ * for tau-leaping, RDME and batches.  These were the fastest measured.  Once a shape is set, every kind of run uses it.  Tau-leaping and
  * RDME kernels take only the block size and check for refills after every
  * step.
  * Results never depend on the launch shape; only speed does.  Not

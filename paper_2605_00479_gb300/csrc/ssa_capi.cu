@@ -57,7 +57,7 @@ int cuda_fail(cudaError_t e, const char *what)
 // direct-method runs use kDirectDefault and tau-leaping, RDME and batches use
 // kOtherDefault (each the fastest measured for its kernels); afterwards all
 // use the shape that was set.
-constexpr ssa::LaunchConfig kDirectDefault = {256, 0, 32};
+constexpr ssa::LaunchConfig kDirectDefault = {0, 0, 32};   // block size chosen per kernel
 constexpr ssa::LaunchConfig kOtherDefault = {128, 0, 16};
 ssa::LaunchConfig g_cfg = kDirectDefault;
 bool g_cfg_set = false;

@@ -9,7 +9,7 @@
 namespace ssa {
 
 struct LaunchConfig {
-    int block;          // threads per block (multiple of 32, <= 256)
+    int block;          // threads per block (multiple of 32, <= 256); 0: chosen per kernel
     int blocks_per_sm;  // 0: as many as occupancy allows
     int slice_pairs;    // step pairs between refill checks
 };
@@ -68,16 +68,27 @@ cudaError_t launch_family(const RunArgs &a, int prec, int sr, LaunchConfig cfg, 
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, cfg.block, 0);
+    int block = cfg.block;
+    if (block == 0) {
+        // 256 threads (eight warps per block pack better under tail compaction)
+        // unless they keep fewer than 85% of the warps 128-thread blocks would
+        int p256 = 0, p128 = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p256, k, 256, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p128, k, 128, 0);
+        if (e != cudaSuccess) return e;
+        block = (p256 * 8 * 100 >= p128 * 4 * 85) ? 256 : 128;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;
     long long grid = (long long)sms * per_sm;
-    const long long need = (a.n_work + cfg.block - 1) / cfg.block;
+    const long long need = (a.n_work + block - 1) / block;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     *grid_out = (int)grid;
-    k<<<(unsigned)grid, (unsigned)cfg.block, 0, stream>>>(a);
+    k<<<(unsigned)grid, (unsigned)block, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

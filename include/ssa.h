@@ -437,6 +437,30 @@ int ssa_surrogate_get_params(ssa_surrogate *s, float *params);
  * [B][4].  Asynchronous on stream. */
 int ssa_surrogate_predict(ssa_surrogate *s, int B, const float *features, float *probs, void *stream);
 
+/*
+ * ssa_surrogate_train -- n_steps AdamW steps (as ssa_surrogate_train_step)
+ * driven from the device: step 0 runs directly, the rest replay one captured
+ * CUDA graph, with the step counters, learning rate and bias corrections kept
+ * in device memory.  No paper counterpart (the surrogate is this project's).
+ *   features, targets  device [n_rows][4] and [n_rows][128] (rows sum to 1)
+ *   batch              rows per step, 1..max_batch; step k trains on rows
+ *                      (k * batch + j) mod n_rows, j < batch -- shuffle the
+ *                      rows beforehand for random minibatches
+ *   lr_max, lr_min     cosine schedule: lr_k = lr_min + (lr_max - lr_min)
+ *                      (1 + cos(pi k / (n_steps - 1))) / 2, in binary64,
+ *                      rounded to binary32
+ *   loss_every, loss_trace  device [ceil(n_steps / loss_every)]: the loss of
+ *                      steps 0, loss_every, 2 loss_every, ...; or NULL
+ *   stream             the caller's stream, or NULL (then a private stream
+ *                      ordered after the legacy default stream)
+ * Each step equals ssa_surrogate_train_step on that minibatch with that
+ * learning rate.  Synchronous: returns once the run has finished.
+ * Errors: SSA_EINVAL, SSA_ECUDA.
+ */
+int ssa_surrogate_train(ssa_surrogate *s, int64_t n_steps, int64_t n_rows, const float *features,
+                        const float *targets, int batch, float lr_max, float lr_min, float weight_decay,
+                        int64_t loss_every, float *loss_trace, void *stream);
+
 /* One AdamW step (beta = 0.9, 0.999; eps = 1e-8; decoupled weight decay on
  * the weights) on the mean cross-entropy of the batch against targets
  * (device [B][128], rows summing to 1).  loss_out: device float or NULL.

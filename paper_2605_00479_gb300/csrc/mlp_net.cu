@@ -129,11 +129,9 @@ __global__ void softmax_ce_kernel(const float *logits, const float *targets, int
 
 // AdamW on the fp32 master parameters (weight decay on weights only; the
 // padding columns of W1 stay zero).
-__global__ void adamw_kernel(float *theta, const float *grad, float *m, float *v, int64_t n, float lr, float beta1,
-                             float beta2, float eps, float wd, float bc1, float bc2)
+__device__ __forceinline__ void adamw_update(int64_t i, float *theta, const float *grad, float *m, float *v, float lr,
+                                             float beta1, float beta2, float eps, float wd, float bc1, float bc2)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     constexpr int64_t b0 = kOffB[0], w1 = kOffW[1], b1 = kOffB[1], w2 = kOffW[2], b2 = kOffB[2], w3 = kOffW[3],
                       b3 = kOffB[3];
     if (i < b0 && (i % 16) >= 4) return;   // W1 padding
@@ -148,6 +146,65 @@ __global__ void adamw_kernel(float *theta, const float *grad, float *m, float *v
     if (!is_bias) t -= lr * wd * t;
     t -= lr * mhat / (sqrtf(vhat) + eps);
     theta[i] = t;
+}
+
+__global__ void adamw_kernel(float *theta, const float *grad, float *m, float *v, int64_t n, float lr, float beta1,
+                             float beta2, float eps, float wd, float bc1, float bc2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) adamw_update(i, theta, grad, m, v, lr, beta1, beta2, eps, wd, bc1, bc2);
+}
+
+// Schedule of a device-driven training run: the step counters and this
+// step's learning rate and bias corrections live in device memory, so one
+// captured step replays unchanged.
+struct TrainSched {
+    long long adam_step;   // AdamW steps taken so far (all runs)
+    long long local;       // step index within this run
+    float lr, bc1, bc2;
+};
+
+constexpr float kBeta1 = 0.9f, kBeta2 = 0.999f, kEps = 1e-8f;
+
+// Same values as the host computes for one train step: the cosine schedule in
+// binary64 rounded to binary32, and 1 - beta^t with beta widened from binary32.
+__global__ void schedule_kernel(TrainSched *sc, long long n_steps, float lr_max, float lr_min)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const long long k = sc->local;
+    const double frac = n_steps > 1 ? (double)k / (double)(n_steps - 1) : 0.0;
+    sc->lr = (float)((double)lr_min + 0.5 * ((double)lr_max - (double)lr_min) * (1.0 + cos(3.141592653589793 * frac)));
+    const long long t = sc->adam_step + 1;
+    sc->bc1 = 1.0f - (float)pow((double)kBeta1, (double)t);
+    sc->bc2 = 1.0f - (float)pow((double)kBeta2, (double)t);
+    sc->adam_step = t;
+}
+
+__global__ void adamw_sched_kernel(float *theta, const float *grad, float *m, float *v, int64_t n,
+                                   const TrainSched *sc, float wd)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) adamw_update(i, theta, grad, m, v, sc->lr, kBeta1, kBeta2, kEps, wd, sc->bc1, sc->bc2);
+}
+
+// Minibatch of step `local`: rows (local * B + j) mod n_rows, one block per row.
+__global__ void gather_batch_kernel(const float *features, const float *targets, int64_t n_rows, int B,
+                                    const TrainSched *sc, float *feat_b, float *targ_b)
+{
+    const int j = blockIdx.x;
+    if (j >= B) return;
+    const int64_t row = (int64_t)((sc->local * (long long)B + j) % n_rows);
+    for (int c = threadIdx.x; c < kBins; c += blockDim.x) targ_b[(int64_t)j * kBins + c] = targets[row * kBins + c];
+    if (threadIdx.x < 4) feat_b[(int64_t)j * 4 + threadIdx.x] = features[row * 4 + threadIdx.x];
+}
+
+// End of a step: record its loss every `every` steps, advance the step index.
+__global__ void finish_step_kernel(const float *loss, TrainSched *sc, long long every, float *trace)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const long long k = sc->local;
+    if (trace && k % every == 0) trace[k / every] = *loss;
+    sc->local = k + 1;
 }
 
 // Normalised histogram of one species' counts per parameter set:
@@ -216,6 +273,8 @@ struct ssa_surrogate {
     float *loss;
     int *error;
     int64_t step;
+    float *feat_b, *targ_b;   // minibatch of a device-driven training run
+    void *sched;              // its TrainSched
     char *arena;
 };
 
@@ -363,6 +422,9 @@ int ssa_surrogate_create(int max_batch, uint64_t seed, ssa_surrogate **out)
     for (int l = 0; l < 3; ++l) sizes[n++] = align256((size_t)Bp * 256 * 2);           // dz_pk
     for (int l = 0; l < 3; ++l) sizes[n++] = align256((size_t)Bp * 256 * 2);           // dzT_pk
     sizes[n++] = 256;                                                                  // loss + error
+    sizes[n++] = align256((size_t)max_batch * 4 * 4);                                  // feat_b
+    sizes[n++] = align256((size_t)max_batch * kBins * 4);                              // targ_b
+    sizes[n++] = align256(sizeof(TrainSched));                                         // sched
     size_t total = 0;
     for (int i = 0; i < n; ++i) total += sizes[i];
     if (cudaMalloc(reinterpret_cast<void **>(&s->arena), total) != cudaSuccess) {
@@ -392,6 +454,10 @@ int ssa_surrogate_create(int max_batch, uint64_t seed, ssa_surrogate **out)
     for (int l = 0; l < 3; ++l) take(&s->dzT_pk[l]);
     s->loss = reinterpret_cast<float *>(p);
     s->error = reinterpret_cast<int *>(p + 16);
+    p += sizes[i++];
+    take(&s->feat_b);
+    take(&s->targ_b);
+    take(&s->sched);
 
     // He-normal weights (std sqrt(2 / fan_in), fan_in = 4 for the first layer), zero biases
     float *h = new (std::nothrow) float[kParams];
@@ -484,6 +550,100 @@ int ssa_surrogate_train_step(ssa_surrogate *s, int B, const float *features, con
     if (e == cudaSuccess && loss_out)
         e = cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? SSA_OK : SSA_ECUDA;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One training step of a device-driven run (all its inputs in device memory).
+cudaError_t scheduled_step(ssa_surrogate *s, int64_t n_steps, int64_t n_rows, const float *features,
+                           const float *targets, int B, float lr_max, float lr_min, float wd, int64_t every,
+                           float *trace, cudaStream_t st)
+{
+    TrainSched *sc = static_cast<TrainSched *>(s->sched);
+    const int Bpad = bpad_of(B);
+    schedule_kernel<<<1, 32, 0, st>>>(sc, (long long)n_steps, lr_max, lr_min);
+    gather_batch_kernel<<<(unsigned)B, 128, 0, st>>>(features, targets, n_rows, B, sc, s->feat_b, s->targ_b);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = forward(s, B, Bpad, s->feat_b, true, st);
+    if (e == cudaSuccess) e = backward(s, B, Bpad, s->targ_b, st);
+    if (e != cudaSuccess) return e;
+    adamw_sched_kernel<<<(unsigned)((kParams + 255) / 256), 256, 0, st>>>(s->theta, s->grad, s->m, s->v, kParams, sc,
+                                                                          wd);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = refresh_all(s, st);
+    if (e == cudaSuccess) {
+        finish_step_kernel<<<1, 32, 0, st>>>(s->loss, sc, (long long)every, trace);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ssa_surrogate_train(ssa_surrogate *s, int64_t n_steps, int64_t n_rows, const float *features,
+                        const float *targets, int batch, float lr_max, float lr_min, float weight_decay,
+                        int64_t loss_every, float *loss_trace, void *stream)
+{
+    if (check_batch(s, batch) != SSA_OK || n_steps < 0 || n_rows < 1 || !features || !targets ||
+        !(lr_max >= 0.0f) || !(lr_min >= 0.0f) || loss_every < 1)
+        return SSA_EINVAL;
+    if (n_steps == 0) return SSA_OK;
+    // a capturable stream: the caller's, or a private one ordered after the
+    // legacy stream (the call synchronises before it returns)
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ev = nullptr;
+    const bool own = st == nullptr;
+    cudaError_t e = cudaSuccess;
+    if (own) {
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, nullptr);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    }
+    TrainSched init;   // copied from pageable memory: staged before the call returns
+    init.adam_step = (long long)s->step;
+    init.local = 0;
+    init.lr = init.bc1 = init.bc2 = 0.0f;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->sched, &init, sizeof(init), cudaMemcpyHostToDevice, st);
+    // step 0 runs directly (it also sets the kernels' attributes); the rest
+    // replay one captured step
+    if (e == cudaSuccess)
+        e = scheduled_step(s, n_steps, n_rows, features, targets, batch, lr_max, lr_min, weight_decay, loss_every,
+                           loss_trace, st);
+    int64_t done = 1;
+    if (e == cudaSuccess && n_steps > 1) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t eg = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (eg == cudaSuccess) {
+            const cudaError_t ec = scheduled_step(s, n_steps, n_rows, features, targets, batch, lr_max, lr_min,
+                                                  weight_decay, loss_every, loss_trace, st);
+            eg = cudaStreamEndCapture(st, &graph);
+            if (eg == cudaSuccess) eg = ec;
+        }
+        if (eg == cudaSuccess) eg = cudaGraphInstantiate(&exec, graph, 0);
+        while (done < n_steps && eg == cudaSuccess) {
+            eg = cudaGraphLaunch(exec, st);
+            if (eg == cudaSuccess) ++done;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (eg != cudaSuccess) cudaGetLastError();   // a step that did not capture runs directly below
+    }
+    for (; done < n_steps && e == cudaSuccess; ++done)
+        e = scheduled_step(s, n_steps, n_rows, features, targets, batch, lr_max, lr_min, weight_decay, loss_every,
+                           loss_trace, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    if (ev) cudaEventDestroy(ev);
+    if (own && st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return SSA_ECUDA;
+    s->step += n_steps;
+    return SSA_OK;
 }
 
 int ssa_surrogate_gradients(ssa_surrogate *s, int B, const float *features, const float *targets, float *grads,

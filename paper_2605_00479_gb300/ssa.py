@@ -53,6 +53,8 @@ SIGNATURES = {
     "ssa_surrogate_get_params": (_I, [_P, _P]),
     "ssa_surrogate_predict": (_I, [_P, _I, _P, _P, _P]),
     "ssa_surrogate_train_step": (_I, [_P, _I, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P]),
+    "ssa_surrogate_train": (_I, [_P, _I64, _I64, _P, _P, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I64,
+                                 _P, _P]),
     "ssa_surrogate_gradients": (_I, [_P, _I, _P, _P, _P, _P]),
     "ssa_surrogate_status": (_I, [_P]),
     "ssa_histogram": (_I, [_P, _I64, _I64, _I, _P, _P]),
@@ -395,6 +397,17 @@ class Surrogate:
         _check(lib().ssa_surrogate_train_step(self._h, features.shape[0], _dev_ptr(features), _dev_ptr(targets),
                                               float(lr), float(weight_decay), _dev_ptr(loss), _stream_ptr(stream)))
 
+    def train(self, features, targets, steps, batch_size, lr_max, lr_min, weight_decay=1e-4, loss_every=1,
+              loss_trace=None, stream=None):
+        """ssa_surrogate_train: `steps` AdamW steps replayed from one captured
+        CUDA graph; step k uses rows (k * batch_size + j) mod n of features /
+        targets (CUDA tensors).  loss_trace: CUDA float tensor of
+        ceil(steps / loss_every) entries, or None.  Synchronous."""
+        _check(lib().ssa_surrogate_train(self._h, int(steps), int(features.shape[0]), _dev_ptr(features),
+                                         _dev_ptr(targets), int(batch_size), float(lr_max), float(lr_min),
+                                         float(weight_decay), int(loss_every), _dev_ptr(loss_trace),
+                                         _stream_ptr(stream)))
+
     def gradients(self, features, targets):
         g = np.empty(self.n_params, dtype=np.float32)
         loss = np.zeros(1, dtype=np.float32)
@@ -438,11 +451,6 @@ def hist_w1(p, q, out=None, stream=None):
 
 
 # ------------------------------------------------------- ensemble statistics
-def _stream_ptr(stream):
-    import torch
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
-
 
 def count_histogram(values, bins, hist=None, clamped=None, stream=None):
     """ssa_count_histogram on a contiguous int32/int16 CUDA tensor; returns

@@ -68,19 +68,18 @@ def simulate_histograms(params, traj_per_set, seed, traj_offset=0, precision="mi
 
 
 def train(net, feats, hists, steps, batch_size, lr_max=2e-3, lr_min=5e-5, weight_decay=1e-4, seed=0):
-    """AdamW with a cosine schedule over random minibatches; returns the loss trace."""
+    """AdamW with a cosine schedule over minibatches of the rows shuffled once
+    (then swept in order), all steps replayed on the device from one captured
+    step; returns the loss trace [(step, loss)] every steps // 50 steps."""
     import torch
     n = feats.shape[0]
     g = torch.Generator(device="cuda").manual_seed(seed)
-    loss = torch.zeros(1, device="cuda")
-    trace = []
-    for step in range(steps):
-        idx = torch.randint(0, n, (batch_size,), device="cuda", generator=g)
-        lr = lr_min + 0.5 * (lr_max - lr_min) * (1 + math.cos(math.pi * step / max(1, steps - 1)))
-        net.train_step(feats[idx], hists[idx], lr, weight_decay, loss=loss)
-        if step % max(1, steps // 50) == 0 or step == steps - 1:
-            trace.append((step, float(loss)))
-    return trace
+    perm = torch.randperm(n, device="cuda", generator=g)
+    f, h = feats[perm].contiguous(), hists[perm].contiguous()
+    every = max(1, steps // 50)
+    losses = torch.full(((steps + every - 1) // every,), float("nan"), device="cuda")
+    net.train(f, h, steps, batch_size, lr_max, lr_min, weight_decay, loss_every=every, loss_trace=losses)
+    return [(k * every, float(v)) for k, v in enumerate(losses.cpu().tolist())]
 
 
 def serve(net, query_params, ref_hist):

@@ -106,3 +106,52 @@ def test_histogram_and_w1_kernels(ssa):
     w = ssa.hist_w1(torch.from_numpy(ref.astype(np.float32)).cuda(), torch.from_numpy(q.astype(np.float32)).cuda())
     from oracle import mlp
     np.testing.assert_allclose(w.cpu().numpy(), mlp.wasserstein_hist(ref, q), rtol=1e-4, atol=1e-5)
+
+
+def test_graph_driven_training_matches_step_by_step(ssa):
+    """ssa_surrogate_train (one captured step replayed) against the same steps
+    issued one by one through ssa_surrogate_train_step with the documented
+    minibatches and learning rates.  Bias gradients are summed with fp32
+    atomics, so the two runs agree up to that summation order: losses to 1e-5
+    relative; parameters to 1e-5 except a small fraction (AdamW's normalised
+    step turns a last-bit difference in a near-zero gradient into a difference
+    of up to 2 lr per step)."""
+    import math
+    n, B, steps, lr_max, lr_min, wd = 3000, 256, 12, 2e-3, 5e-5, 1e-4
+    rng = np.random.default_rng(3)
+    feats = torch.from_numpy(rng.normal(size=(n, 4)).astype(np.float32)).cuda()
+    t = rng.random((n, 128)).astype(np.float32)
+    t /= t.sum(axis=1, keepdims=True)
+    targs = torch.from_numpy(t).cuda()
+    a = ssa.Surrogate(B, seed=7)
+    b = ssa.Surrogate(B, seed=7)
+    np.testing.assert_array_equal(a.get_params(), b.get_params())
+    trace = torch.full((steps,), float("nan"), device="cuda")
+    a.train(feats, targs, steps, B, lr_max, lr_min, wd, loss_every=1, loss_trace=trace)
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for k in range(steps):
+        rows = torch.from_numpy((k * B + np.arange(B)) % n).cuda()
+        lr = lr_min + 0.5 * (lr_max - lr_min) * (1 + math.cos(math.pi * k / (steps - 1)))
+        b.train_step(feats[rows], targs[rows], lr, wd, loss=loss)
+        losses.append(float(loss))
+    np.testing.assert_allclose(trace.cpu().numpy(), np.array(losses, np.float32), rtol=1e-5)
+    assert losses[-1] < losses[0]
+    pa, pb = a.get_params(), b.get_params()
+    d = np.abs(pa - pb)
+    assert np.mean(d <= 1e-5 + 1e-5 * np.abs(pb)) > 0.99
+    assert d.max() <= 2 * lr_max * steps
+
+
+def test_graph_driven_training_trace_every_and_validation(ssa):
+    n, B = 1000, 128
+    feats = torch.zeros((n, 4), device="cuda")
+    targs = torch.full((n, 128), 1.0 / 128, device="cuda")
+    s = ssa.Surrogate(B, seed=1)
+    trace = torch.full((4,), float("nan"), device="cuda")
+    s.train(feats, targs, 10, B, 1e-3, 1e-3, 0.0, loss_every=3, loss_trace=trace)   # steps 0, 3, 6, 9
+    assert torch.isfinite(trace).all()
+    with pytest.raises(ssa.SSAError):
+        s.train(feats, targs, 5, B + 1, 1e-3, 1e-3)      # batch above max_batch
+    with pytest.raises(ssa.SSAError):
+        s.train(feats, targs, 5, B, 1e-3, 1e-3, loss_every=0)

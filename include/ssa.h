@@ -287,15 +287,27 @@ int ssa_set_launch_config(int threads_per_block, int blocks_per_sm, int slice_pa
 int ssa_set_tail_compaction(int enabled);
 
 /*
+ * ssa_set_tail_lock_limit -- bound on one wait for a block's hand-off lock in
+ * subsequent direct-method launches: at most `spins` attempts (0, the
+ * default, means 2^22 attempts, under a second).  A wait that runs out is
+ * counted and decides nothing; small limits exist to exercise that path.
+ * Results never depend on it: stranded trajectories are resumed at the end
+ * of the block (below).  Errors: SSA_EINVAL (spins < 0).
+ */
+int ssa_set_tail_lock_limit(int spins);
+
+/*
  * ssa_tail_stats -- synchronises the current device, then reports, for all
  * direct-method launches of this process on it so far, the trajectories moved
- * between warps by tail compaction (*moved) and the hand-off lock waits that
- * gave up (*lock_timeouts; each wait is bounded, under a second).  A nonzero
- * *lock_timeouts means a launch may have left trajectories unfinished: treat
- * its outputs as invalid.  Either pointer may be NULL.
+ * between warps by tail compaction (*moved), the hand-off lock waits that
+ * gave up (*lock_timeouts; each wait is bounded) and the trajectories a
+ * block resumed from its pool after all its warps had left (*resumed: a warp
+ * whose lock wait gave up can leave while records wait for it; once every
+ * warp is out, warp 0 runs whatever the pool still holds, so outputs stay
+ * complete and identical).  Any pointer may be NULL.
  * Errors: SSA_ECUDA.
  */
-int ssa_tail_stats(int64_t *moved, int64_t *lock_timeouts);
+int ssa_tail_stats(int64_t *moved, int64_t *lock_timeouts, int64_t *resumed);
 
 /*
  * Batched heterogeneous runs: several groups, each a model with a sweep of
@@ -368,9 +380,14 @@ void ssa_batch_destroy(ssa_batch *batch);
  * For callers that cannot allocate device memory while they simulate:
  * programs whose device memory belongs to another allocator or is held to a
  * fixed budget after start-up, and real-time or embedded loops that forbid
- * allocation on their hot path.  The call makes no cudaMalloc, cudaFree or
- * other allocating call, on the device or the host; the caller passes the
- * inputs and owns the outputs.  Its scratch (the work-queue counter and the
+ * allocation on their hot path.  A successful call makes no cudaMalloc,
+ * cudaFree or other allocating call, on the device or the host; the caller
+ * passes the inputs and owns the outputs.  Two exceptions: the first call on
+ * a device and the first call in each precision / rounding mode may load
+ * code (lazy module loading, the symbol lookup below), which can allocate
+ * device memory, so allocation-sensitive callers make one warm-up call in
+ * every mode they use; and the error path formats its message into
+ * heap-allocated host memory.  Its scratch (the work-queue counter and the
  * per-set tables) lives in one static device array of
  * SSA_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
  * the process exits.
@@ -388,6 +405,11 @@ void ssa_batch_destroy(ssa_batch *batch);
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) for that device; make that first call before any
  *    stream capture.
+ *  - The per-set tables are staged from a host buffer that lives only during
+ *    the call, so a call on a stream that is capturing is refused with
+ *    SSA_EINVAL.
+ *  - n_sets above SSA_NOALLOC_SCRATCH_BYTES / 8, or n_sets * traj_per_set
+ *    beyond int64, is rejected with SSA_EINVAL before any table is sized.
  *  - Every call shares the one array, which keeps the previous call's
  *    contents (the call resets what must start at zero).  Calls whose work
  *    overlaps on the GPU (other streams, other threads) race on it:
@@ -473,6 +495,15 @@ int ssa_surrogate_train_step(ssa_surrogate *s, int B, const float *features, con
 int ssa_surrogate_gradients(ssa_surrogate *s, int B, const float *features, const float *targets,
                             float *grads, float *loss);
 
+/* Optimiser state after synchronising: fp32 master parameters, AdamW first
+ * and second moments and the gradient of the last step (host [param_count]
+ * each, any may be NULL) and the number of AdamW steps taken (t of the bias
+ * corrections 1 - beta^t; NULL allowed).  AdamW (Loshchilov & Hutter,
+ * decoupled weight decay) is not in the paper; hyperparameters beta1 = 0.9f,
+ * beta2 = 0.999f, eps = 1e-8f, decay on weights only.  Synchronous. */
+int ssa_surrogate_get_state(ssa_surrogate *s, float *theta, float *m, float *v, float *grad,
+                            int64_t *adam_steps);
+
 /* Synchronise and report a tensor-core pipeline timeout (SSA_ETIMEDOUT) if a
  * GEMM's bounded wait gave up since creation. */
 int ssa_surrogate_status(ssa_surrogate *s);
@@ -520,11 +551,74 @@ int ssa_hist_ks_w1(const uint64_t *ha, const uint64_t *hb, int bins, double *out
 int ssa_dwell_histogram(const void *series, int elem_bytes, int K, int64_t n, int64_t k_stride, uint64_t *hist,
                         void *stream);
 
+/*
+ * ssa_round16 -- one 16-bit rounding of the engine applied to an array: the
+ * rounding that ends every reduced-precision operation (paper Sec. 3.1
+ * formats, Sec. 3.3 stochastic rounding: round up with probability
+ * (x - x-)/(x+ - x-)).  The kernels' own device functions are used, so this
+ * is the engine's rounding contract, checkable value by value.
+ *
+ * x: device [n] binary32 inputs.  format: 0 binary16, 1 bfloat16.
+ * rounding: 0 round to nearest even (rbits unused, may be NULL), 1 SR.
+ * rbits: device [n] random words; SR uses the low 16 bits (half = 0) or the
+ * high 16 bits (half = 1) of each word, as operation slots 2i and 2i+1 of a
+ * step do.  binary16 uses the low 13 of those 16 bits aligned with the most
+ * significant discarded bit (13-bit resolution, also for subnormal results),
+ * bfloat16 all 16; a magnitude rounded past the largest finite value becomes
+ * infinity.  out: device [n] results widened to binary32 (exact).
+ * Asynchronous on `stream`.  Errors: SSA_EINVAL, SSA_ECUDA.
+ */
+int ssa_round16(const float *x, const uint32_t *rbits, int64_t n, int format, int rounding, int half,
+                float *out, void *stream);
+
 /* Tensor-core GEMM check: D (device [M][N] fp32) = A (device [M][K] bf16,
  * row-major) times B (device [N][K] bf16, row-major) transposed.
  * N in 16..256 and a multiple of 16; K a multiple of 16 (of 256 above 256).
  * Synchronous; SSA_ETIMEDOUT if a bounded wait gave up. */
 int ssa_mlp_gemm_bf16(int M, int N, int K, const uint16_t *A, const uint16_t *B, float *D, void *stream);
+
+/*
+ * Stage checks of the surrogate's training step (no paper counterpart): the
+ * fused kernels of ssa_surrogate_train_step on caller inputs, so each can be
+ * compared element by element with a CPU reference.  Synchronous; device
+ * pointers; row-major.
+ *
+ * ssa_mlp_gemm_epi: acc = A (bf16 [M][K]) times B (bf16 [N][K]) transposed,
+ * fp32 accumulation in tensor memory, then epilogue
+ *   0  fout = acc                                   (weight gradients)
+ *   1  fout = z = acc + bias;  hout = bf16(gelu(z)) (hidden layer forward)
+ *   2  fout = acc + bias                            (logits)
+ *   3  d = acc * gelu'(zin) (zin fp32 [M][N]); hout = bf16(d);
+ *      bias_grad[n] += sum over rows of d (fp32 atomics)  (hidden backward)
+ * gelu(z) = z Phi(z) (exact form, Phi the normal CDF).  Sizes as
+ * ssa_mlp_gemm_bf16.  Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA,
+ * SSA_ETIMEDOUT (a bounded wait gave up).
+ *
+ * ssa_mlp_softmax_xent: per row of logits (fp32 [B][128]): without targets,
+ * probs = softmax; with targets (fp32 [B][128], rows summing to 1),
+ * dz = bf16((softmax - targets) / B) (bf16 [B][128]), bias_grad[k] += sum of
+ * the unrounded (softmax - targets) / B over rows, *loss += mean
+ * cross-entropy (caller zeroes the accumulators).  Errors: SSA_EINVAL,
+ * SSA_ENOMEM, SSA_ECUDA.
+ */
+int ssa_mlp_gemm_epi(int epi, int M, int N, int K, const uint16_t *A, const uint16_t *B, const float *bias,
+                     const float *zin, float *fout, uint16_t *hout, float *bias_grad, void *stream);
+int ssa_mlp_softmax_xent(int B, const float *logits, const float *targets, float *probs, uint16_t *dz,
+                         float *bias_grad, float *loss, void *stream);
+
+/*
+ * ssa_mlp_set_wait_test -- failure detection of the tensor-core GEMM (no
+ * paper counterpart).  Every wait of the GEMM (operands landed, MMAs done) is
+ * bounded; when one runs out, the kernel records an error word, lets its own
+ * copies and MMAs in flight land (bounded), frees its tensor memory and
+ * returns, and the caller sees SSA_ETIMEDOUT (ssa_mlp_gemm_bf16,
+ * ssa_surrogate_status).  This setting makes that happen on purpose for all
+ * later GEMMs of the process: withhold 1 issues no operand loads, withhold 2
+ * no MMAs, so that wait never completes; spin_limit is the number of polls
+ * per wait (0: 2^22).  (0, 0) restores normal operation.  Not synchronised
+ * with launches from other threads.  Errors: SSA_EINVAL.
+ */
+int ssa_mlp_set_wait_test(int withhold, int spin_limit);
 
 /* Thread-local description of the last error on the calling thread. */
 const char *ssa_last_error(void);

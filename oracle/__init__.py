@@ -143,6 +143,28 @@ def run(model, x0, n_traj, t_end, sample_times, precision="fp64", rounding="rn",
     return {"snapshots": out, "status": status, "n_events": nev, "t_final": tf}
 
 
+def trace_step(model, x0, step, precision="fp64", rounding="rn", normalise=False, seed=0, g=0, t_end=1e30):
+    """Inputs and intermediates of direct-method step ``step`` of trajectory
+    ``g`` (the oracle's own arithmetic, recorded as it runs): a dict with n,
+    t (before the step), x (before), a (propensities), S (partial sums), a0,
+    u1, u2, E, U2, tau, target, t_new, mu; None if the trajectory ended
+    earlier.  For tests that recompute one step independently."""
+    M, N = np.asarray(model["order"]).shape
+    buf = np.zeros(160, dtype=np.float64)
+    L = lib()
+    L.oracle_trace_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    L.oracle_trace_step(_p(buf), int(step))
+    try:
+        run(model, x0, 1, t_end, [t_end], precision, rounding, normalise, seed, max_events=int(step) + 1, g0=g)
+    finally:
+        L.oracle_trace_step(None, -1)
+    if buf[0] != 1.0:
+        return None
+    return {"n": int(buf[1]), "t": buf[2], "x": buf[3:3 + N].astype(np.int64), "a": buf[16:16 + M].copy(),
+            "S": buf[48:48 + M].copy(), "a0": buf[80], "u1": buf[81], "u2": buf[82], "E": buf[83], "U2": buf[84],
+            "tau": buf[85], "target": buf[86], "t_new": buf[87], "mu": int(buf[88])}
+
+
 def _run_chunk(args):
     kwargs = dict(args)
     return run(**kwargs)

@@ -8,6 +8,14 @@ histogram p:  L = -(1/B) sum_b sum_k p_bk log softmax(z_b)_k.
 
 GELU is the exact form x * Phi(x) with Phi the standard normal CDF.
 
+The optimiser is AdamW (Loshchilov & Hutter, "Decoupled Weight Decay
+Regularization", ICLR 2019, Algorithm 2 with the Adam bias corrections):
+m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;  m^ = m/(1-b1^t);
+v^ = v/(1-b2^t);  theta = theta - lr wd theta - lr m^/(sqrt(v^) + eps),
+the decay term only on weight matrices (not biases), and the W1 padding
+columns never touched.  The paper trains no network; this is the
+surrogate's optimiser.
+
 Parameter vector (float32 on the GPU, float64 here), in this order:
   W1 [256][16] (input columns 4..15 are padding and stay zero), b1 [256],
   W2 [256][256], b2 [256], W3 [256][256], b3 [256], W4 [128][256], b4 [128].
@@ -97,23 +105,33 @@ def forward(theta, features, bf16=False):
     return softmax(logits), {"acts": acts, "zs": zs, "logits": logits, "P": P}
 
 
-def loss_and_grad(theta, features, targets, bf16=False):
-    """Cross-entropy loss and its gradient with respect to theta."""
+def loss_and_grad(theta, features, targets, bf16=False, trace=None):
+    """Cross-entropy loss and its gradient with respect to theta.
+
+    With a dict as ``trace``, the backward pass's intermediates are stored in
+    it: q (probabilities), cache (the forward cache), and per layer l the
+    pre-activation gradient dz{l} (l = 4 for the logits), its stored copy
+    dzr{l} and the back-propagated dh{l} (l = 1..3)."""
     r = bf16_round if bf16 else (lambda a: a)
     q, c = forward(theta, features, bf16)
     P = c["P"]
     B = features.shape[0]
     loss = float(-(targets * np.log(np.maximum(q, 1e-300))).sum() / B)
+    tr = trace if trace is not None else {}
+    tr["q"], tr["cache"] = q, c
     g = {}
     dz = (q - targets) / B                      # d loss / d logits
     g["b4"] = dz.sum(axis=0)
     dz_r = r(dz)
+    tr["dz4"], tr["dzr4"] = dz, dz_r
     g["W4"] = dz_r.T @ c["acts"][3]
     dh = dz_r @ r(P["W4"])
     for l in (3, 2, 1):
+        tr[f"dh{l}"] = dh
         dz = dh * gelu_grad(c["zs"][l - 1])
         g[f"b{l}"] = dz.sum(axis=0)
         dz_r = r(dz)
+        tr[f"dz{l}"], tr[f"dzr{l}"] = dz, dz_r
         g[f"W{l}"] = dz_r.T @ c["acts"][l - 1]
         if l > 1:
             dh = dz_r @ r(P[f"W{l}"])
@@ -124,3 +142,30 @@ def loss_and_grad(theta, features, targets, bf16=False):
 def wasserstein_hist(p, q):
     """W1 between two histograms on the integers 0..K-1 (rows)."""
     return np.abs(np.cumsum(p, axis=-1) - np.cumsum(q, axis=-1)).sum(axis=-1)
+
+
+def decay_mask():
+    """1 where AdamW applies weight decay (weight matrices), 0 for biases."""
+    return np.concatenate([np.full(int(np.prod(shape)), 1.0 if name.startswith("W") else 0.0)
+                           for name, shape in SHAPES])
+
+
+def active_mask():
+    """False for the W1 padding columns 4..15, which AdamW leaves alone."""
+    a = np.ones(N_PARAMS, dtype=bool)
+    a[:256 * 16] = np.tile(np.arange(16) < 4, 256)
+    return a
+
+
+def adamw_step(theta, grad, m, v, t, lr, wd, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One AdamW step (t = index of this step, starting at 1), float64.
+    Returns (theta, m, v) after the step."""
+    theta, grad, m, v = (np.asarray(a, dtype=np.float64) for a in (theta, grad, m, v))
+    act = active_mask()
+    m_new = np.where(act, beta1 * m + (1.0 - beta1) * grad, m)
+    v_new = np.where(act, beta2 * v + (1.0 - beta2) * grad * grad, v)
+    m_hat = m_new / (1.0 - beta1 ** t)
+    v_hat = v_new / (1.0 - beta2 ** t)
+    step = lr * m_hat / (np.sqrt(v_hat) + eps)
+    th = theta - lr * wd * decay_mask() * theta - step
+    return np.where(act, th, theta), m_new, v_new

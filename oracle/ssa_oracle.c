@@ -520,6 +520,48 @@ typedef struct {
     int64_t max_events;
 } runp;
 
+/* ------------------------------------------------------------------------ */
+/* Step trace (test hook, single-threaded use): the inputs and intermediates  */
+/* of step `g_trace_step` of the next trajectory simulated, so that a test    */
+/* can recompute that one step independently.  Layout of the buffer:          */
+/*   [0] 1 when recorded, [1] n, [2] t before the step, [3..3+N) x before,   */
+/*   [16..16+M) propensities, [48..48+M) partial sums S_1..S_M, [80] a0,     */
+/*   [81] u1, [82] u2, [83] E, [84] U2 (the u2 the target uses), [85] tau,   */
+/*   [86] target, [87] t_new, [88] mu.  Values widened to binary64 (exact).  */
+/* ------------------------------------------------------------------------ */
+static double *g_trace = NULL;
+static int64_t g_trace_step = -1;
+
+void oracle_trace_step(double *buf, int64_t step)
+{
+    g_trace = buf;
+    g_trace_step = step;
+}
+
+static void trace_record(const omodel *md, int64_t n, double t, const int32_t *x, const double *a,
+                         const double *S, double u1, double u2, double E, double U2, double tau, double target,
+                         double t_new, int mu)
+{
+    double *b = g_trace;
+    g_trace = NULL;
+    b[0] = 1.0;
+    b[1] = (double)n;
+    b[2] = t;
+    for (int i = 0; i < md->N && i < 13; ++i) b[3 + i] = (double)x[i];
+    for (int j = 0; j < md->M && j < 32; ++j) { b[16 + j] = a[j]; b[48 + j] = S[j]; }
+    b[80] = S[md->M - 1];
+    b[81] = u1; b[82] = u2; b[83] = E; b[84] = U2; b[85] = tau; b[86] = target; b[87] = t_new;
+    b[88] = (double)mu;
+}
+
+static void trace_f32(const omodel *md, int64_t n, float t, const int32_t *x, const float *a, const float *S,
+                      float u1, float u2, float E, float U2, float tau, float target, float t_new, int mu)
+{
+    double ad[OR_MAX_M], Sd[OR_MAX_M];
+    for (int j = 0; j < md->M; ++j) { ad[j] = a[j]; Sd[j] = S[j]; }
+    trace_record(md, n, t, x, ad, Sd, u1, u2, E, U2, tau, target, t_new, mu);
+}
+
 static void traj_f64(const omodel *md, const runp *rp, word_stream *ws, int32_t *x,
                      const sink *S, uint32_t *status, int64_t *n_events, double *t_final)
 {
@@ -555,6 +597,7 @@ static void traj_f64(const omodel *md, const runp *rp, word_stream *ws, int32_t 
         int mu = -1;
         for (int j = 0; j < M; ++j) if (Ssum[j] > target) { mu = j; break; }
         if (mu < 0) for (int j = M - 1; j >= 0; --j) if (a[j] > 0.0) { mu = j; break; }
+        if (g_trace && n == g_trace_step) trace_record(md, n, t, x, a, Ssum, u1, u2, E, u2, tau, target, t_new, mu);
         const int negative = apply_event(md, mu, x, status);
         t = t_new;
         n += 1;
@@ -616,6 +659,7 @@ static void traj_f32_mixed(const omodel *md, const runp *rp, word_stream *ws, wo
         int mu = -1;
         for (int j = 0; j < M; ++j) if (Ssum[j] > target) { mu = j; break; }
         if (mu < 0) for (int j = M - 1; j >= 0; --j) if (a[j] > 0.0f) { mu = j; break; }
+        if (g_trace && n == g_trace_step) trace_f32(md, n, t, x, a, Ssum, u1, u2, E, u2, tau, target, t_new, mu);
         const int negative = apply_event(md, mu, x, status);
         t = t_new;
         n += 1;
@@ -682,6 +726,7 @@ static void traj_uniform(const omodel *md, const runp *rp, word_stream *ws, word
         int mu = -1;
         for (int j = 0; j < M; ++j) if (Ssum[j] > target) { mu = j; break; }
         if (mu < 0) for (int j = M - 1; j >= 0; --j) if (a[j] > 0.0f) { mu = j; break; }
+        if (g_trace && n == g_trace_step) trace_f32(md, n, t, x, a, Ssum, u1, u2, E, U2, tau, target, t_new, mu);
         const int negative = apply_event(md, mu, x, status);
         t = t_new;
         n += 1;

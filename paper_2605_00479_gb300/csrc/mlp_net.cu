@@ -516,6 +516,20 @@ int ssa_surrogate_get_params(ssa_surrogate *s, float *params)
                                                                                                          : SSA_ECUDA;
 }
 
+int ssa_surrogate_get_state(ssa_surrogate *s, float *theta, float *m, float *v, float *grad, int64_t *adam_steps)
+{
+    if (!s) return SSA_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SSA_ECUDA;
+    const size_t bytes = sizeof(float) * kParams;
+    cudaError_t e = cudaSuccess;
+    if (theta) e = cudaMemcpy(theta, s->theta, bytes, cudaMemcpyDeviceToHost);
+    if (m && e == cudaSuccess) e = cudaMemcpy(m, s->m, bytes, cudaMemcpyDeviceToHost);
+    if (v && e == cudaSuccess) e = cudaMemcpy(v, s->v, bytes, cudaMemcpyDeviceToHost);
+    if (grad && e == cudaSuccess) e = cudaMemcpy(grad, s->grad, bytes, cudaMemcpyDeviceToHost);
+    if (adam_steps) *adam_steps = s->step;
+    return e == cudaSuccess ? SSA_OK : SSA_ECUDA;
+}
+
 int ssa_surrogate_predict(ssa_surrogate *s, int B, const float *features, float *probs, void *stream)
 {
     if (check_batch(s, B) != SSA_OK || !features || !probs) return SSA_EINVAL;
@@ -665,6 +679,30 @@ int ssa_surrogate_status(ssa_surrogate *s)
     if (cudaDeviceSynchronize() != cudaSuccess) return SSA_ECUDA;
     if (cudaMemcpy(&h, s->error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SSA_ECUDA;
     return h ? SSA_ETIMEDOUT : SSA_OK;
+}
+
+int ssa_mlp_softmax_xent(int B, const float *logits, const float *targets, float *probs, uint16_t *dz,
+                         float *bias_grad, float *loss, void *stream)
+{
+    if (B < 1 || B > (1 << 20) || !logits) return SSA_EINVAL;
+    if (!targets && !probs) return SSA_EINVAL;
+    if (targets && (!dz || !bias_grad || !loss)) return SSA_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int Bpad = bpad_of(B);
+    uint8_t *pk = nullptr;
+    const size_t half = (size_t)Bpad * kBins * 2;
+    if (targets && cudaMallocAsync(reinterpret_cast<void **>(&pk), 2 * half, st) != cudaSuccess) return SSA_ENOMEM;
+    softmax_ce_kernel<<<(Bpad * 32 + 255) / 256, 256, 0, st>>>(logits, targets, B, Bpad, probs, pk,
+                                                               pk ? pk + half : nullptr, bias_grad, loss);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && targets) {
+        const int64_t n = (int64_t)B * kBins;
+        mlp::unpack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pk, B, kBins, dz);
+        e = cudaGetLastError();
+    }
+    if (pk) cudaFreeAsync(pk, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? SSA_OK : SSA_ECUDA;
 }
 
 int ssa_histogram(const int32_t *counts, int64_t n_sets, int64_t traj_per_set, int bins, float *hist, void *stream)

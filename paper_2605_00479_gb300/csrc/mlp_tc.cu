@@ -47,10 +47,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: false after kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// Bounded wait: false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
 {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -168,11 +168,13 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
     const uint32_t idesc = instr_desc_bf16_f32(kTileM, nt);
     const uint32_t rg_bytes = (uint32_t)g.kchunk * 16u;   // one 8-row group of one stage
     const uint32_t stage_bytes = (uint32_t)(kTileM + nt) * (uint32_t)g.kchunk * 2u;
+    const uint32_t limit = g.spin_limit ? g.spin_limit : kSpinLimit;
     int err = ERR_NONE;
+    bool loads_pending = false, mma_pending = false;   // issued work whose completion was not seen
     int ch = 0;
     for (; ch < n_chunks; ++ch) {
         const uint32_t parity = (uint32_t)(ch & 1);
-        if (warp == 0) {
+        if (warp == 0 && g.withhold != 1) {
             if (lane == 0) mbar_expect_tx(&bars[0], stage_bytes);
             __syncwarp();
             const int colA = g.a_col0 + ch * g.kchunk, colB = g.b_col0 + ch * g.kchunk;
@@ -189,12 +191,14 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
                 }
             }
         }
-        if (!mbar_wait(&bars[0], parity)) {
+        loads_pending = g.withhold != 1;
+        if (!__syncthreads_and(mbar_wait(&bars[0], parity, limit))) {
             err = ERR_LOAD_TIMEOUT;
             break;
         }
+        loads_pending = false;
         tc_fence_after();
-        if (tid == 0) {
+        if (tid == 0 && g.withhold != 2) {
             const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
             for (int s = 0; s < g.kchunk / 16; ++s) {
                 const uint64_t ad = smem_desc(a0 + (uint32_t)s * 256u, 128u, rg_bytes);
@@ -203,13 +207,15 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
             }
             mma_commit(&bars[1]);
         }
+        mma_pending = g.withhold != 2;
         __syncwarp();
-        if (!mbar_wait(&bars[1], parity)) {
+        if (!__syncthreads_and(mbar_wait(&bars[1], parity, limit))) {
             err = ERR_MMA_TIMEOUT;
             break;
         }
+        mma_pending = false;
     }
-    const bool ok = __syncthreads_and(err == ERR_NONE) != 0;
+    const bool ok = err == ERR_NONE;   // the same in every thread
     tc_fence_after();
 
     if (ok) {
@@ -260,9 +266,10 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
         }
     } else {
         if (tid == 0) atomicExch(g.error, err);
-        // let our own copies and MMAs drain (bounded) before tensor memory is freed
-        mbar_wait(&bars[0], (uint32_t)(ch & 1));
-        mbar_wait(&bars[1], (uint32_t)(ch & 1));
+        // let our own copies and MMAs still in flight land (bounded) before the
+        // CTA frees its tensor memory and leaves its shared memory
+        if (loads_pending) mbar_wait(&bars[0], (uint32_t)(ch & 1), kSpinLimit);
+        if (mma_pending) mbar_wait(&bars[1], (uint32_t)(ch & 1), kSpinLimit);
     }
     tc_fence_before();
     __syncthreads();
@@ -290,11 +297,24 @@ __global__ void pack_bf16_kernel(const uint16_t *src, int rows, int cols, int ld
     *reinterpret_cast<uint4 *>(dst + packed_offset(r, c0, C)) = v;
 }
 
+namespace {
+int g_withhold = 0;
+uint32_t g_spin_limit = 0;
+}  // namespace
+
+void set_wait_test(int withhold, uint32_t spin_limit)
+{
+    g_withhold = withhold;
+    g_spin_limit = spin_limit;
+}
+
 cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s)
 {
     // Shared memory also caps how many CTAs share an SM: request enough that
     // their tensor-memory columns (ncols each) never exceed the SM's 512.
     GemmArgs a = g;
+    a.withhold = g_withhold;
+    a.spin_limit = g_spin_limit;
     a.ntile = (g.N >= 128 && g.N % 64 == 0) ? 64 : g.N;   // column tiles per row tile: N / ntile
     const int ncols = a.ntile <= 32 ? 32 : (a.ntile <= 64 ? 64 : (a.ntile <= 128 ? 128 : 256));
     const size_t per_sm = 233472, reserve = 1024;
@@ -310,6 +330,16 @@ cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Packed bf16 [rows_pad][C] -> row-major [rows][C] (one thread per element).
+__global__ void unpack_bf16_kernel(const uint8_t *src, int rows, int C, uint16_t *dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * C) return;
+    const int64_t r = i / C;
+    const int c = (int)(i % C);
+    dst[i] = *reinterpret_cast<const uint16_t *>(src + packed_offset(r, c, C));
+}
+
 cudaError_t launch_pack(const uint16_t *src, int rows, int cols, int ld, uint8_t *dst, int rows_pad, int C,
                         cudaStream_t s)
 {
@@ -320,18 +350,34 @@ cudaError_t launch_pack(const uint16_t *src, int rows, int cols, int ld, uint8_t
 
 }  // namespace mlp
 
-// ------------------------------------------------------------ C ABI test entry
-extern "C" int ssa_mlp_gemm_bf16(int M, int N, int K, const uint16_t *A, const uint16_t *B, float *D, void *stream)
+// ------------------------------------------------------------ C ABI test entries
+extern "C" int ssa_mlp_set_wait_test(int withhold, int spin_limit)
 {
+    if (withhold < 0 || withhold > 2 || spin_limit < 0) return SSA_EINVAL;
+    mlp::set_wait_test(withhold, (uint32_t)spin_limit);
+    return SSA_OK;
+}
+
+extern "C" int ssa_mlp_gemm_epi(int epi, int M, int N, int K, const uint16_t *A, const uint16_t *B,
+                                const float *bias, const float *zin, float *fout, uint16_t *hout, float *bias_grad,
+                                void *stream)
+{
+    if (epi < mlp::EPI_STORE_F32 || epi > mlp::EPI_HIDDEN_BWD) return SSA_EINVAL;
     if (M < 1 || N < 16 || N > mlp::kMaxN || N % 16 != 0 || K < 16 || K % 16 != 0 || (K > 256 && K % 256 != 0) ||
-        !A || !B || !D)
+        !A || !B)
         return SSA_EINVAL;
+    const bool need_f = epi != mlp::EPI_HIDDEN_BWD, need_h = epi == mlp::EPI_HIDDEN_FWD || epi == mlp::EPI_HIDDEN_BWD;
+    if ((need_f && !fout) || (need_h && !hout)) return SSA_EINVAL;
+    if ((epi == mlp::EPI_HIDDEN_FWD || epi == mlp::EPI_LOGITS) && !bias) return SSA_EINVAL;
+    if (epi == mlp::EPI_HIDDEN_BWD && (!zin || !bias_grad)) return SSA_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int Mpad = (M + mlp::kTileM - 1) / mlp::kTileM * mlp::kTileM;
     const size_t a_bytes = (size_t)Mpad * K * 2, b_bytes = (size_t)N * K * 2;
+    const size_t h_bytes = need_h ? (size_t)Mpad * N * 2 : 0;
     uint8_t *buf = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&buf), a_bytes + b_bytes + 256, s) != cudaSuccess) return SSA_ENOMEM;
-    int *err = reinterpret_cast<int *>(buf + a_bytes + b_bytes);
+    if (cudaMallocAsync(reinterpret_cast<void **>(&buf), a_bytes + b_bytes + h_bytes + 256, s) != cudaSuccess)
+        return SSA_ENOMEM;
+    int *err = reinterpret_cast<int *>(buf + a_bytes + b_bytes + h_bytes);
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = mlp::launch_pack(A, M, K, K, buf, Mpad, K, s);
     if (e == cudaSuccess) e = mlp::launch_pack(B, N, K, K, buf + a_bytes, N, K, s);
@@ -346,15 +392,30 @@ extern "C" int ssa_mlp_gemm_bf16(int M, int N, int K, const uint16_t *A, const u
     g.N = N;
     g.K = K;
     g.kchunk = K > 256 ? 256 : K;
-    g.epi = mlp::EPI_STORE_F32;
-    g.fout = D;
+    g.epi = epi;
+    g.bias = bias;
+    g.zin = zin;
+    g.fout = fout;
     g.ld_fout = N;
+    g.pk_out = need_h ? buf + a_bytes + b_bytes : nullptr;
+    g.bias_grad = bias_grad;
     g.error = err;
     if (e == cudaSuccess) e = mlp::launch_gemm(g, s);
+    if (e == cudaSuccess && need_h) {
+        const int64_t n = (int64_t)M * N;
+        mlp::unpack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g.pk_out, M, N, hout);
+        e = cudaGetLastError();
+    }
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFreeAsync(buf, s);
     if (e != cudaSuccess) return SSA_ECUDA;
     return herr ? SSA_ETIMEDOUT : SSA_OK;
+}
+
+extern "C" int ssa_mlp_gemm_bf16(int M, int N, int K, const uint16_t *A, const uint16_t *B, float *D, void *stream)
+{
+    if (!D) return SSA_EINVAL;
+    return ssa_mlp_gemm_epi(mlp::EPI_STORE_F32, M, N, K, A, B, nullptr, nullptr, D, nullptr, nullptr, stream);
 }

@@ -16,7 +16,8 @@
 // commits them to a second mbarrier; four warps read the accumulator with
 // tcgen05.ld and run a fused epilogue.  Every wait is bounded: on timeout the
 // kernel records an error code, waits (bounded) for its own work in flight,
-// frees its tensor memory and returns.
+// frees its tensor memory and returns.  Whether a wait ran out is decided for
+// the whole CTA at once (__syncthreads_and), so all threads leave together.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -57,7 +58,13 @@ struct GemmArgs {
     int pkT_cols;
     float *bias_grad;          // [N], accumulated with atomics
     int *error;                // device error word (0 = ok)
+    uint32_t spin_limit;       // polls per bounded wait (0: kSpinLimit)
+    int withhold;              // failure-detection test: 1 no operand loads, 2 no MMAs (their waits run out)
 };
+
+// Failure-detection test setting applied by launch_gemm to every later GEMM
+// (withhold 0 and spin_limit 0: normal operation).
+void set_wait_test(int withhold, uint32_t spin_limit);
 
 __host__ __device__ constexpr uint32_t instr_desc_bf16_f32(int M, int N)
 {
@@ -74,6 +81,7 @@ __host__ __device__ inline int64_t packed_offset(int64_t r, int64_t c, int64_t C
 }
 
 cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s);
+__global__ void unpack_bf16_kernel(const uint8_t *src, int rows, int C, uint16_t *dst);
 cudaError_t launch_pack(const uint16_t *src, int rows, int cols, int ld, uint8_t *dst, int rows_pad, int C,
                         cudaStream_t s);
 

@@ -8,6 +8,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -64,12 +65,14 @@ bool g_cfg_set = false;
 
 ssa::LaunchConfig other_cfg() { return g_cfg_set ? g_cfg : kOtherDefault; }
 bool g_tail_compaction = true;
+int g_tail_lock_spins = 0;   // 0: the kernels' default bound
 
 }  // namespace
 
 // Counters of the direct-method kernels' tail compaction on each device:
-// [0] trajectories moved between warps, [1] lock waits that gave up.
-__device__ unsigned long long g_tail_counters[2];
+// [0] trajectories moved between warps, [1] lock waits that gave up,
+// [2] trajectories resumed from the pool at the end of a block.
+__device__ unsigned long long g_tail_counters[3];
 
 namespace {
 
@@ -266,6 +269,7 @@ int launch_run(const ssa_model *model, int64_t n_work, int64_t stride, uint64_t 
     }
     a->queue_head = head;
     a->tail_stats = tail_counters();
+    a->lock_spins = g_tail_lock_spins;
     int grid = 0;
     e = launcher_for(model->family)(*a, precision, rounding, normalise ? 1 : 0, g_cfg, s, &grid);
     cudaError_t e2 = cudaFreeAsync(head, s);
@@ -306,14 +310,22 @@ int ssa_set_tail_compaction(int enabled)
     return SSA_OK;
 }
 
-int ssa_tail_stats(int64_t *moved, int64_t *lock_timeouts)
+int ssa_set_tail_lock_limit(int spins)
 {
-    unsigned long long c[2] = {0, 0};
+    if (spins < 0) return fail(SSA_EINVAL, "spins must be >= 0");
+    g_tail_lock_spins = spins;
+    return SSA_OK;
+}
+
+int ssa_tail_stats(int64_t *moved, int64_t *lock_timeouts, int64_t *resumed)
+{
+    unsigned long long c[3] = {0, 0, 0};
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpyFromSymbol(c, g_tail_counters, sizeof(c));
     if (e != cudaSuccess) return cuda_fail(e, "tail counters");
     if (moved) *moved = (int64_t)c[0];
     if (lock_timeouts) *lock_timeouts = (int64_t)c[1];
+    if (resumed) *resumed = (int64_t)c[2];
     return SSA_OK;
 }
 
@@ -1054,6 +1066,9 @@ extern "C" {
 size_t ssa_sweep_noalloc_scratch_bytes(int n_species, int n_reactions, int64_t n_sets)
 {
     if (n_sets < 0) return 0;
+    // every set needs at least 8 bytes, so larger counts can never fit (and
+    // the table sizes below could wrap around)
+    if (n_sets > (int64_t)SSA_NOALLOC_SCRATCH_BYTES / 8) return SIZE_MAX;
     const GroupTables T = group_tables(n_sets, n_reactions, n_species);
     return 256 + T.total();
 }
@@ -1066,7 +1081,22 @@ int ssa_sweep_run_noalloc(const ssa_model *model, int64_t n_sets, int64_t traj_p
 {
     if (!model) return fail(SSA_EINVAL, "model is NULL");
     if (n_sets < 1 || traj_per_set < 0) return fail(SSA_EINVAL, "n_sets >= 1 and traj_per_set >= 0");
+    if (n_sets > (int64_t)SSA_NOALLOC_SCRATCH_BYTES / 8)
+        return fail(SSA_EINVAL, "n_sets = %lld cannot fit the static scratch of %d bytes", (long long)n_sets,
+                    SSA_NOALLOC_SCRATCH_BYTES);
+    if (traj_per_set > INT64_MAX / n_sets) return fail(SSA_EINVAL, "n_sets * traj_per_set overflows");
     if (!x0) return fail(SSA_EINVAL, "x0 is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        // The per-set tables are staged from a stack buffer that is gone when
+        // the call returns, so a captured copy would replay garbage: refuse.
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const cudaError_t ce = cudaStreamIsCapturing(s, &cs);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamIsCapturing");
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(SSA_EINVAL, "stream is capturing: ssa_sweep_run_noalloc stages its tables from host memory "
+                                    "that does not outlive the call and cannot be captured");
+    }
     const ssa_model &m = *model;
     const size_t need = ssa_sweep_noalloc_scratch_bytes(m.N, m.M, n_sets);
     if (need > (size_t)SSA_NOALLOC_SCRATCH_BYTES)
@@ -1094,7 +1124,6 @@ int ssa_sweep_run_noalloc(const ssa_model *model, int64_t n_sets, int64_t traj_p
     void *scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc != SSA_OK) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned long long *head = static_cast<unsigned long long *>(scratch);
     const GroupTables T = group_tables(n_sets, m.M, m.N);
     double *d_cp = reinterpret_cast<double *>(static_cast<char *>(scratch) + 256);
@@ -1149,6 +1178,7 @@ int ssa_sweep_run_noalloc(const ssa_model *model, int64_t n_sets, int64_t traj_p
     a.t_final = t_final;
     a.queue_head = head;
     a.tail_stats = tail_counters();
+    a.lock_spins = g_tail_lock_spins;
 
     // the scratch keeps the previous call's contents: reset the queue counter
     cudaError_t e = cudaMemsetAsync(head, 0, sizeof(unsigned long long), s);

@@ -96,7 +96,8 @@ struct RunArgs {
     int64_t *n_events;
     double *t_final;
     unsigned long long *queue_head;    // zero before launch
-    unsigned long long *tail_stats;    // [trajectories moved, lock waits given up]; null: no tail compaction
+    unsigned long long *tail_stats;    // [moved, lock waits given up, resumed at block end]; null: no tail compaction
+    int lock_spins;                    // bound on one hand-off lock wait (0: kPoolLockSpins)
 };
 
 // ------------------------------------------------------------------ Philox
@@ -891,6 +892,12 @@ __device__ __noinline__ void ssa_step_general(const RunArgs &a, Lane<GeneralMode
 //    under the lock).  Hence whenever the pool holds records some live warp
 //    remains, and it takes them into idle lanes at its next refill check.
 //  * Each warp leaves once, so a trajectory moves at most warps - 1 times.
+//  * A lock wait that gives up (counted) decides nothing: a busy warp runs
+//    on, an idle one leaves with its `live` bit still set, so records given
+//    to the pool afterwards may find no taker.  Therefore, once every warp
+//    of the block has left the loop, warp 0 checks the pool and resumes
+//    whatever it still holds (counted), so no trajectory is ever left
+//    unfinished and results never depend on give-ups.
 constexpr int kPoolCap = 96;              // records held at once
 constexpr int kPoolWarps = 8;             // warps per block (blockDim <= 256)
 constexpr int kPoolLockSpins = 1 << 22;   // bound on the lock wait (under a second)
@@ -922,9 +929,9 @@ __device__ __forceinline__ void pool_init(TailPool<Model, PREC> *p)
     }
 }
 
-__device__ __forceinline__ bool pool_acquire(int *lock)
+__device__ __forceinline__ bool pool_acquire(int *lock, int spins)
 {
-    for (int i = 0; i < kPoolLockSpins; ++i) {
+    for (int i = 0; i < spins; ++i) {
         if (atomicCAS(lock, 0, 1) == 0) {
             __threadfence_block();
             return true;
@@ -943,7 +950,7 @@ __device__ __forceinline__ void pool_release(int *lock)
 // Lane 0's decision at a pool visit (kept out of line: it runs only after the
 // queue has drained).  Returns (timeout << 31) | (op << 24) | (base << 12) | num.
 static __device__ __noinline__ unsigned pool_decide(int *lock, int *count_p, unsigned *live_p, int *act, int w, int nb,
-                                             unsigned long long *stats)
+                                             unsigned long long *stats, int spins)
 {
     volatile int *vcount = count_p;
     volatile unsigned *vlive = live_p;
@@ -956,7 +963,7 @@ static __device__ __noinline__ unsigned pool_decide(int *lock, int *count_p, uns
     const bool maybe = nb == 0 || (cnt > 0 && nb < 32) || (nb <= room && cnt + nb <= kPoolCap);
     vact[w] = nb;
     if (!maybe) return 0u;
-    if (!pool_acquire(lock)) {
+    if (!pool_acquire(lock, spins)) {
         atomicAdd(&stats[1], 1ull);
         return 1u << 31;
     }
@@ -1001,14 +1008,15 @@ __device__ __forceinline__ bool pool_visit(const RunArgs &a, TailPool<Model, PRE
     // 0 nothing, 1 take records, 2 give trajectories away, 3 leave (idle, pool empty)
     int op = 0, base = 0, num = 0, ok = 1;
     if (lane == 0) {
-        const unsigned r = pool_decide(&p->lock, &p->count, &p->live, p->act, w, nb, a.tail_stats);
+        const unsigned r = pool_decide(&p->lock, &p->count, &p->live, p->act, w, nb, a.tail_stats,
+                                       a.lock_spins > 0 ? a.lock_spins : kPoolLockSpins);
         ok = (int)(r >> 31) ^ 1;
         op = (int)((r >> 24) & 0x7Fu);
         base = (int)((r >> 12) & 0xFFFu);
         num = (int)(r & 0xFFFu);
     }
     ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
-    if (!ok) return nb == 0;   // lock wait gave up (counted): leave only if idle
+    if (!ok) return nb == 0;   // lock wait gave up (counted): leave only if idle (records: block-end resume)
     op = __shfl_sync(0xFFFFFFFFu, op, 0);
     if (op == 0) return false;
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
@@ -1119,9 +1127,18 @@ __global__ void __launch_bounds__(256, SSA_MIN_BLOCKS) ssa_kernel(const __grid_c
     using P = typename ModeTraits<PREC>::P;
     __shared__ P smp[kMaxK];
     __shared__ TailPool<Model, PREC> pool;
-    if (a.tail_stats) pool_init(&pool);
+    const bool pooled = a.tail_stats != nullptr;
+    if (pooled) pool_init(&pool);
     load_samples<PREC>(a.samples, a.K, smp);   // ends with __syncthreads
-    run_queue<Model, PREC, SR>(a, smp, to_time<PREC>(a.t_end), a.tail_stats ? &pool : nullptr);
+    for (int pass = 0;; ++pass) {
+        run_queue<Model, PREC, SR>(a, smp, to_time<PREC>(a.t_end), pooled ? &pool : nullptr);
+        if (!pooled || pass > 0) break;
+        // every warp has left the loop: records stranded by a lock wait that
+        // gave up are resumed by warp 0 (the pool no longer changes)
+        __syncthreads();
+        if (pool.count == 0 || threadIdx.x >= 32) break;
+        if (threadIdx.x == 0) atomicAdd(&a.tail_stats[2], (unsigned long long)pool.count);
+    }
 }
 
 // Several groups (heterogeneous structures and parameter sweeps), one queue

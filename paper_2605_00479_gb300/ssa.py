@@ -36,7 +36,8 @@ SIGNATURES = {
                           _P]),
     "ssa_set_launch_config": (_I, [_I, _I, _I]),
     "ssa_set_tail_compaction": (_I, [_I]),
-    "ssa_tail_stats": (_I, [ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "ssa_set_tail_lock_limit": (_I, [_I]),
+    "ssa_tail_stats": (_I, [ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "ssa_batch_create": (_I, [_I, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, ctypes.POINTER(_P)]),
     "ssa_batch_launch": (_I, [_P, _P]),
     "ssa_batch_autotune": (_I, [_P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -46,6 +47,9 @@ SIGNATURES = {
     "ssa_sweep_run_noalloc": (_I, [_P, _I64, _I64, _P, _P, _P, _U64, _D, _I, _P, _I, _I, _I, _U64, _I64, _I,
                                    _P, _P, _P, _P, _P]),
     "ssa_mlp_gemm_bf16": (_I, [_I, _I, _I, _P, _P, _P, _P]),
+    "ssa_mlp_set_wait_test": (_I, [_I, _I]),
+    "ssa_mlp_gemm_epi": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ssa_mlp_softmax_xent": (_I, [_I, _P, _P, _P, _P, _P, _P, _P]),
     "ssa_surrogate_param_count": (_I64, []),
     "ssa_surrogate_create": (_I, [_I, _U64, ctypes.POINTER(_P)]),
     "ssa_surrogate_destroy": (None, [_P]),
@@ -56,7 +60,9 @@ SIGNATURES = {
     "ssa_surrogate_train": (_I, [_P, _I64, _I64, _P, _P, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I64,
                                  _P, _P]),
     "ssa_surrogate_gradients": (_I, [_P, _I, _P, _P, _P, _P]),
+    "ssa_surrogate_get_state": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_I64)]),
     "ssa_surrogate_status": (_I, [_P]),
+    "ssa_round16": (_I, [_P, _P, _I64, _I, _I, _I, _P, _P]),
     "ssa_histogram": (_I, [_P, _I64, _I64, _I, _P, _P]),
     "ssa_hist_w1": (_I, [_P, _P, _I64, _I, _P, _P]),
     "ssa_count_histogram": (_I, [_P, _I, _I64, _I, _P, _P, _P]),
@@ -154,12 +160,18 @@ def set_tail_compaction(enabled=True):
     _check(lib().ssa_set_tail_compaction(1 if enabled else 0))
 
 
+def set_tail_lock_limit(spins=0):
+    """Bound on one hand-off lock wait of tail compaction (0: the default)."""
+    _check(lib().ssa_set_tail_lock_limit(int(spins)))
+
+
 def tail_stats():
-    """(trajectories moved between warps, lock waits given up) so far on the
-    current device; synchronises it."""
-    moved, timeouts = _I64(0), _I64(0)
-    _check(lib().ssa_tail_stats(ctypes.byref(moved), ctypes.byref(timeouts)))
-    return int(moved.value), int(timeouts.value)
+    """(trajectories moved between warps, lock waits given up, trajectories
+    resumed at the end of a block) so far on the current device; synchronises
+    it."""
+    moved, timeouts, resumed = _I64(0), _I64(0), _I64(0)
+    _check(lib().ssa_tail_stats(ctypes.byref(moved), ctypes.byref(timeouts), ctypes.byref(resumed)))
+    return int(moved.value), int(timeouts.value), int(resumed.value)
 
 
 def _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision, rounding, normalise, seed,
@@ -415,6 +427,13 @@ class Surrogate:
                                              _np_ptr(g), _np_ptr(loss)))
         return float(loss[0]), g
 
+    def get_state(self):
+        """ssa_surrogate_get_state: (theta, m, v, grad, adam_steps), host arrays."""
+        arrs = [np.empty(self.n_params, dtype=np.float32) for _ in range(4)]
+        t = ctypes.c_int64(0)
+        _check(lib().ssa_surrogate_get_state(self._h, *[_np_ptr(a) for a in arrs], ctypes.byref(t)))
+        return (*arrs, int(t.value))
+
     def status(self):
         _check(lib().ssa_surrogate_status(self._h))
 
@@ -428,6 +447,17 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+def round16(x, rbits=None, fmt="f16", rounding="rn", half=0, out=None, stream=None):
+    """ssa_round16 on CUDA tensors: x float32, rbits int32/uint32 words (SR);
+    returns the rounded values widened to float32."""
+    import torch
+    if out is None:
+        out = torch.empty_like(x, dtype=torch.float32)
+    _check(lib().ssa_round16(_dev_ptr(x), _dev_ptr(rbits), int(x.numel()), {"f16": 0, "bf16": 1}[fmt],
+                             {"rn": 0, "sr": 1}[rounding], int(half), _dev_ptr(out), _stream_ptr(stream)))
+    return out
 
 
 def histogram(counts, n_sets, traj_per_set, bins=128, hist=None, stream=None):

@@ -34,19 +34,20 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def run_noalloc(ssa, model, rates, hill, x0, traj_per_set, offset, t_end, samples, prec, rnd, seed, cap):
+def run_noalloc(ssa, model, rates, hill, x0, traj_per_set, offset, t_end, samples, prec, rnd, seed, cap,
+                normalise=False, state_bytes=4):
     S = x0.shape[0]
     n = S * traj_per_set
     K = len(samples)
     dev = torch.device("cuda", torch.cuda.current_device())
-    out = torch.full((K, model.N, n), -7, dtype=torch.int32, device=dev)
+    out = torch.full((K, model.N, n), -7, dtype=torch.int16 if state_bytes == 2 else torch.int32, device=dev)
     st = torch.full((n,), -7, dtype=torch.int32, device=dev)
     ev = torch.full((n,), -7, dtype=torch.int64, device=dev)
     tf = torch.full((n,), -7.0, dtype=torch.float64, device=dev)
     smp = np.ascontiguousarray(samples, dtype=np.float64)
     rc = ssa.lib().ssa_sweep_run_noalloc(
         model.handle, S, traj_per_set, _ptr(rates), _ptr(hill), _ptr(x0), offset, float(t_end), K, _ptr(smp),
-        ssa.PRECISION[prec], ssa.ROUNDING[rnd], 0, seed, cap, 4, ctypes.c_void_p(out.data_ptr()),
+        ssa.PRECISION[prec], ssa.ROUNDING[rnd], int(normalise), seed, cap, state_bytes, ctypes.c_void_p(out.data_ptr()),
         ctypes.c_void_p(st.data_ptr()), ctypes.c_void_p(ev.data_ptr()), ctypes.c_void_p(tf.data_ptr()),
         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 0, ssa.lib().ssa_last_error()
@@ -55,7 +56,8 @@ def run_noalloc(ssa, model, rates, hill, x0, traj_per_set, offset, t_end, sample
             "t_final": tf.cpu().numpy()}
 
 
-def run_existing(ssa, model_dict, rates, hill, x0, traj_per_set, offset, t_end, samples, prec, rnd, seed, cap):
+def run_existing(ssa, model_dict, rates, hill, x0, traj_per_set, offset, t_end, samples, prec, rnd, seed, cap,
+                 normalise=False, state_bytes=4):
     parts = []
     for q in range(x0.shape[0]):
         md = dict(model_dict)
@@ -66,8 +68,8 @@ def run_existing(ssa, model_dict, rates, hill, x0, traj_per_set, offset, t_end, 
             h[:, :2] = hill[q]
             md["hill"] = h
         m = ssa.Model.from_dict(md)
-        r = ssa.ensemble_run(m, traj_per_set, x0[q], t_end, samples, prec, rnd, False, seed, cap,
-                             traj_offset=offset + q * traj_per_set)
+        r = ssa.ensemble_run(m, traj_per_set, x0[q], t_end, samples, prec, rnd, normalise, seed, cap,
+                             state_bytes=state_bytes, traj_offset=offset + q * traj_per_set)
         torch.cuda.synchronize()
         parts.append({k: v.cpu().numpy() for k, v in r.items()})
     return {k: np.concatenate([p[k] for p in parts], axis=-1) for k in parts[0]}
@@ -116,3 +118,73 @@ def test_noalloc_rejects_sweeps_beyond_the_scratch(ssa):
                                          0, 1000, 4, ctypes.c_void_p(8), ctypes.c_void_p(8), None, None, None)
     assert rc == ssa.SSA_EINVAL
     assert b"scratch" in ssa.lib().ssa_last_error()
+
+
+def test_noalloc_single_set_normalised_reservoirs_and_int16(ssa):
+    """Paths the sweep test above leaves out: with one set the kernel reads the
+    scalar rate, Hill and x0 fields (filled from set 0); with normalise=1 every
+    set folds its own reservoir counts into c' (Sec. 4.2 rescaling), so sets
+    that differ only in A and B differ in their rates; int16 storage clamps the
+    reservoir columns.  Each call is compared with ssa_ensemble_run."""
+    sch = P.schlogl()
+    m = ssa.Model.from_dict(sch)
+    x0 = np.ascontiguousarray(P.schlogl_x0(sch), dtype=np.int32)
+    # one set, normalised, int32
+    args = (None, None, x0[None, :], 300, 77, 2.0, [0.5, 1.0, 2.0], "mixed_bf16", "sr", 5, 10**6)
+    a = run_noalloc(ssa, m, *args, normalise=True)
+    b = run_existing(ssa, sch, *args, normalise=True)
+    same(a, b)
+    # four sets with different reservoir counts, normalised, int16 storage
+    xs = np.tile(x0, (4, 1))
+    xs[:, 1] = [100000, 90000, 110000, 100000]
+    xs[:, 2] = [200000, 210000, 190000, 180000]
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    args = (None, None, xs, 64, 4000, 1.0, [0.5, 1.0], "uniform_f16", "sr", 9, 10**6)
+    a = run_noalloc(ssa, m, *args, normalise=True, state_bytes=2)
+    b = run_existing(ssa, sch, *args, normalise=True, state_bytes=2)
+    same(a, b)
+    assert a["snapshots"].dtype == np.int16
+    # the reservoir columns are clamped to int16 and flagged
+    assert np.all(a["snapshots"][:, 1:, :] == 32767) and np.all(a["status"] & 4)
+    # different reservoirs mean different folded rates: the sets' X columns differ
+    X = a["snapshots"][-1, 0, :].reshape(4, 64).astype(np.float64)
+    assert len({round(float(r.mean()), 3) for r in X}) > 1
+
+
+def test_noalloc_refuses_a_capturing_stream(ssa):
+    """The per-set tables are staged from host memory that lives only for the
+    call, so a captured call would replay stale tables: it is refused."""
+    tel = P.telegraph()
+    m = ssa.Model.from_dict(tel)
+    x0 = np.ascontiguousarray(np.tile(P.TELEGRAPH_X0, (2, 1)), dtype=np.int32)
+    smp = np.array([1.0])
+    n = 2 * 32
+    out = torch.zeros((1, m.N, n), dtype=torch.int32, device="cuda")
+    st = torch.zeros(n, dtype=torch.int32, device="cuda")
+    # warm-up call on this device outside capture (it looks up the scratch address)
+    run_noalloc(ssa, m, None, None, x0, 32, 0, 1.0, [1.0], "mixed_f16", "rn", 1, 1000)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    rc = None
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            rc = ssa.lib().ssa_sweep_run_noalloc(m.handle, 2, 32, None, None, _ptr(x0), 0, 1.0, 1, _ptr(smp), 2, 0,
+                                                 0, 1, 1000, 4, ctypes.c_void_p(out.data_ptr()),
+                                                 ctypes.c_void_p(st.data_ptr()), None, None,
+                                                 ctypes.c_void_p(s.cuda_stream))
+        finally:
+            g.capture_end()
+    assert rc == ssa.SSA_EINVAL
+    assert b"capturing" in ssa.lib().ssa_last_error()
+
+
+def test_noalloc_rejects_set_counts_that_would_wrap(ssa):
+    tel = ssa.Model.from_dict(P.telegraph())
+    assert ssa.lib().ssa_sweep_noalloc_scratch_bytes(3, 4, 2**62) == 2**64 - 1
+    x0 = np.zeros((1, 3), np.int32)
+    smp = np.array([1.0])
+    for S, T in ((2**61, 1), (2, 2**62)):
+        rc = ssa.lib().ssa_sweep_run_noalloc(tel.handle, S, T, None, None, _ptr(x0), 0, 1.0, 1, _ptr(smp), 2, 0,
+                                             0, 0, 1000, 4, ctypes.c_void_p(8), ctypes.c_void_p(8), None, None, None)
+        assert rc == ssa.SSA_EINVAL

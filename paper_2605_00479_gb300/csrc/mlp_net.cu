@@ -167,7 +167,8 @@ struct TrainSched {
 constexpr float kBeta1 = 0.9f, kBeta2 = 0.999f, kEps = 1e-8f;
 
 // Same values as the host computes for one train step: the cosine schedule in
-// binary64 rounded to binary32, and 1 - beta^t with beta widened from binary32.
+// binary64 rounded to binary32, and 1 - beta^t in binary64 (beta widened from
+// binary32) rounded once.
 __global__ void schedule_kernel(TrainSched *sc, long long n_steps, float lr_max, float lr_min)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -175,8 +176,8 @@ __global__ void schedule_kernel(TrainSched *sc, long long n_steps, float lr_max,
     const double frac = n_steps > 1 ? (double)k / (double)(n_steps - 1) : 0.0;
     sc->lr = (float)((double)lr_min + 0.5 * ((double)lr_max - (double)lr_min) * (1.0 + cos(3.141592653589793 * frac)));
     const long long t = sc->adam_step + 1;
-    sc->bc1 = 1.0f - (float)pow((double)kBeta1, (double)t);
-    sc->bc2 = 1.0f - (float)pow((double)kBeta2, (double)t);
+    sc->bc1 = (float)(1.0 - pow((double)kBeta1, (double)t));
+    sc->bc2 = (float)(1.0 - pow((double)kBeta2, (double)t));
     sc->adam_step = t;
 }
 
@@ -555,8 +556,10 @@ int ssa_surrogate_train_step(ssa_surrogate *s, int B, const float *features, con
     if (e != cudaSuccess) return SSA_ECUDA;
     s->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;
-    const float bc1 = 1.0f - (float)std::pow((double)b1, (double)s->step);
-    const float bc2 = 1.0f - (float)std::pow((double)b2, (double)s->step);
+    // 1 - beta^t in binary64, rounded once: subtracting a rounded beta^t from
+    // 1 in binary32 would cancel (about 250 ulp off for beta2 at t = 4)
+    const float bc1 = (float)(1.0 - std::pow((double)b1, (double)s->step));
+    const float bc2 = (float)(1.0 - std::pow((double)b2, (double)s->step));
     adamw_kernel<<<(unsigned)((kParams + 255) / 256), 256, 0, st>>>(s->theta, s->grad, s->m, s->v, kParams, lr, b1, b2,
                                                                    1e-8f, weight_decay, bc1, bc2);
     e = cudaGetLastError();

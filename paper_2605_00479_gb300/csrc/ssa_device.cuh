@@ -896,8 +896,9 @@ __device__ __noinline__ void ssa_step_general(const RunArgs &a, Lane<GeneralMode
 //    on, an idle one leaves with its `live` bit still set, so records given
 //    to the pool afterwards may find no taker.  Therefore, once every warp
 //    of the block has left the loop, warp 0 checks the pool and resumes
-//    whatever it still holds (counted), so no trajectory is ever left
-//    unfinished and results never depend on give-ups.
+//    whatever it still holds (counted), as the only live warp (so it never
+//    gives work away), and no trajectory is ever left unfinished: results
+//    never depend on give-ups.
 constexpr int kPoolCap = 96;              // records held at once
 constexpr int kPoolWarps = 8;             // warps per block (blockDim <= 256)
 constexpr int kPoolLockSpins = 1 << 22;   // bound on the lock wait (under a second)
@@ -1137,7 +1138,14 @@ __global__ void __launch_bounds__(256, SSA_MIN_BLOCKS) ssa_kernel(const __grid_c
         // gave up are resumed by warp 0 (the pool no longer changes)
         __syncthreads();
         if (pool.count == 0 || threadIdx.x >= 32) break;
-        if (threadIdx.x == 0) atomicAdd(&a.tail_stats[2], (unsigned long long)pool.count);
+        if (threadIdx.x == 0) {
+            atomicAdd(&a.tail_stats[2], (unsigned long long)pool.count);
+            // warp 0 is the only warp left: with stale `live` bits of warps
+            // that left after a give-up, it could hand its work back to the
+            // pool and leave; as the sole live warp it only takes records
+            pool.live = 1u;
+        }
+        __syncwarp();
     }
 }
 

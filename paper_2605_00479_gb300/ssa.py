@@ -312,7 +312,9 @@ class Batch:
     ``self.outputs[g]``."""
 
     def __init__(self, groups, t_end, sample_times, precision="mixed_f16", rounding="rn", normalise=False, seed=0,
-                 max_events=10**9, state_bytes=4):
+                 max_events=10**9, state_bytes=4, host_outputs=False):
+        """host_outputs: outputs in page-locked host memory (written by the
+        kernel directly) instead of device memory."""
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         st = np.ascontiguousarray(np.atleast_1d(sample_times), dtype=np.float64)
@@ -330,11 +332,13 @@ class Batch:
             hill = G.get("hill")
             hill = None if hill is None else np.ascontiguousarray(hill, dtype=np.float64).reshape(S, m.M, 2)
             n = S * T
-            o = {"snapshots": torch.empty((K, m.N, n), dtype=torch.int16 if state_bytes == 2 else torch.int32,
-                                          device=dev),
-                 "status": torch.empty(n, dtype=torch.int32, device=dev),
-                 "n_events": torch.empty(n, dtype=torch.int64, device=dev),
-                 "t_final": torch.empty(n, dtype=torch.float64, device=dev)}
+            def alloc(shape, dtype):
+                if host_outputs:
+                    return torch.empty(shape, dtype=dtype).pin_memory()
+                return torch.empty(shape, dtype=dtype, device=dev)
+            o = {"snapshots": alloc((K, m.N, n), torch.int16 if state_bytes == 2 else torch.int32),
+                 "status": alloc(n, torch.int32), "n_events": alloc(n, torch.int64),
+                 "t_final": alloc(n, torch.float64)}
             self.outputs.append(o)
             self._keep += [x0, rates, hill, m]
             arr[g] = BatchGroup(m.handle, S, T, _np_ptr(rates), _np_ptr(hill), _np_ptr(x0), int(G.get("traj_offset", 0)),

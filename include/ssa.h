@@ -137,7 +137,15 @@ int ssa_model_kernel_family(const ssa_model *model);
  *   max_events    event cap per trajectory, >= 0
  *   state_bytes   4 (int32 snapshots) or 2 (int16; values are clamped and
  *                 flagged SSA_TRAJ_STATE_RANGE when out of range)
- *   out           device [K][N][n_traj], trajectory index fastest
+ *   out_species   bit i set: species i is stored in the snapshots; 0 means
+ *                 every species.  A run stores only what the caller needs --
+ *                 e.g. not the reservoir species that normalisation holds
+ *                 fixed -- and its snapshot stream shrinks accordingly.  The
+ *                 simulation itself never depends on it; int16 clamping (and
+ *                 its status bit) applies to stored species only.  Bits
+ *                 beyond n_species are rejected (SSA_EINVAL).
+ *   out           device [K][Ns][n_traj], Ns = number of stored species (in
+ *                 ascending species order), trajectory index fastest
  *   traj_status   device [n_traj] status bits
  *   n_events      device [n_traj] events fired per trajectory, or NULL
  *   t_final       device [n_traj] time of the last event (widened), or NULL
@@ -149,8 +157,8 @@ int ssa_model_kernel_family(const ssa_model *model);
 int ssa_ensemble_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset,
                      const int32_t *x0, double t_end, int n_samples, const double *sample_times,
                      int precision, int rounding, int normalise, uint64_t seed,
-                     int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
-                     int64_t *n_events, double *t_final, void *stream);
+                     int64_t max_events, int state_bytes, uint32_t out_species, void *out,
+                     uint32_t *traj_status, int64_t *n_events, double *t_final, void *stream);
 
 /*
  * ssa_ensemble_run_host -- ssa_ensemble_run with HOST output buffers;
@@ -159,9 +167,12 @@ int ssa_ensemble_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offse
  * NULL).
  *  - If every given output is page-locked host memory that the current
  *    device addresses under the same pointer (cudaHostAlloc, or
- *    cudaHostRegister with mapping; unified addressing), the kernel writes
- *    the results straight into it as the ensemble runs -- on Grace-Blackwell
- *    over NVLink-C2C -- with no device buffers and no copy afterwards.
+ *    cudaHostRegister with mapping; unified addressing) and the snapshot
+ *    stream is sparse (at most 0.05 snapshot bytes per event, events
+ *    estimated as a0(x0) * t_end), the kernel writes the results straight
+ *    into it as the ensemble runs -- on Grace-Blackwell over NVLink-C2C --
+ *    with no device buffers and no copy afterwards.  A denser stream would
+ *    cross the link one small store at a time, so it is staged instead.
  *  - Otherwise the call stages the results in device buffers and copies them
  *    back after the kernel.  The device buffers come from a memory pool
  *    private to the library that keeps its reservation between calls (the
@@ -172,8 +183,8 @@ int ssa_ensemble_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offse
 int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_offset,
                           const int32_t *x0, double t_end, int n_samples, const double *sample_times,
                           int precision, int rounding, int normalise, uint64_t seed,
-                          int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
-                          int64_t *n_events, double *t_final, void *stream);
+                          int64_t max_events, int state_bytes, uint32_t out_species, void *out,
+                          uint32_t *traj_status, int64_t *n_events, double *t_final, void *stream);
 
 /*
  * ssa_tau_run -- explicit tau-leaping with a fixed leap (the approximate
@@ -516,6 +527,14 @@ int ssa_histogram(const int32_t *counts, int64_t n_sets, int64_t traj_per_set, i
 /* w1 (device [rows]) = sum_b |CDF_p(b) - CDF_q(b)| for histograms p, q
  * (device [rows][bins]): the Wasserstein-1 distance on the integers. */
 int ssa_hist_w1(const float *p, const float *q, int64_t rows, int bins, float *w1, void *stream);
+
+/* Expected Wasserstein-1 distance between a law and the empirical histogram
+ * of n_draws independent draws from it, per row of p (device [rows][bins],
+ * rows summing to 1): sum over b < bins-1 of sqrt(2 F(b)(1 - F(b)) / (pi n)),
+ * the normal approximation of E|F_n(b) - F(b)| (F the cumulative law).  The
+ * surrogate's judge uses it as the sampling noise of a small SSA ensemble.
+ * No paper counterpart.  Asynchronous.  Errors: SSA_EINVAL, SSA_ECUDA. */
+int ssa_hist_w1_noise(const float *p, int64_t rows, int bins, double n_draws, float *out, void *stream);
 
 /*
  * On-device ensemble statistics (the comparisons of Sec. 4: two-sample

@@ -42,7 +42,7 @@ def lib():
         L.oracle_run.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P,
                                  ctypes.c_int64, ctypes.c_uint64, ctypes.c_double,
                                  ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                 ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, P, P, P, P]
+                                 ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32, P, P, P, P]
         for name in ("oracle_f32_to_f16_array", "oracle_f32_to_bf16_array"):
             getattr(L, name).argtypes = [P, ctypes.c_int64, ctypes.c_int, P, P]
         L.oracle_f16_to_f32_array.argtypes = [P, ctypes.c_int64, P]
@@ -108,7 +108,7 @@ def log_f64(x):
 
 # ---------------------------------------------------------------- the SSA
 def run(model, x0, n_traj, t_end, sample_times, precision="fp64", rounding="rn", normalise=False,
-        seed=0, max_events=10**9, state_bytes=4, g0=0):
+        seed=0, max_events=10**9, state_bytes=4, g0=0, out_species=0):
     """Simulate trajectories g0 .. g0+n_traj-1 of ``model`` on the oracle.
 
     ``model`` is a mapping with numpy arrays ``order`` [M,N], ``stoich`` [M,N],
@@ -128,7 +128,8 @@ def run(model, x0, n_traj, t_end, sample_times, precision="fp64", rounding="rn",
     x0 = np.ascontiguousarray(x0, dtype=np.int32)
     st = np.ascontiguousarray(sample_times, dtype=np.float64)
     K = st.size
-    out = np.zeros((K, N, n_traj), dtype=np.int16 if state_bytes == 2 else np.int32)
+    Ns = N if not out_species else bin(int(out_species)).count("1")
+    out = np.zeros((K, Ns, n_traj), dtype=np.int16 if state_bytes == 2 else np.int32)
     status = np.zeros(n_traj, dtype=np.uint32)
     nev = np.zeros(n_traj, dtype=np.int64)
     tf = np.zeros(n_traj, dtype=np.float64)
@@ -136,7 +137,7 @@ def run(model, x0, n_traj, t_end, sample_times, precision="fp64", rounding="rn",
     rnd = ROUNDINGS[rounding] if isinstance(rounding, str) else int(rounding)
     rc = lib().oracle_run(N, M, _p(order), _p(stoich), _p(rate), _p(law), _p(hill), _p(const), _p(x0),
                           int(n_traj), int(g0), float(t_end), K, _p(st), prec, rnd, int(bool(normalise)),
-                          int(seed) & 0xFFFFFFFFFFFFFFFF, int(max_events), int(state_bytes),
+                          int(seed) & 0xFFFFFFFFFFFFFFFF, int(max_events), int(state_bytes), int(out_species),
                           _p(out), _p(status), _p(nev), _p(tf))
     if rc != 0:
         raise ValueError("oracle_run rejected its arguments")

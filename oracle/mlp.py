@@ -169,3 +169,12 @@ def adamw_step(theta, grad, m, v, t, lr, wd, beta1=0.9, beta2=0.999, eps=1e-8):
     step = lr * m_hat / (np.sqrt(v_hat) + eps)
     th = theta - lr * wd * decay_mask() * theta - step
     return np.where(act, th, theta), m_new, v_new
+
+
+def expected_w1_noise(p, n):
+    """Expected W1 between the law p (rows, on the integers 0..K-1) and the
+    empirical histogram of n draws from it: sum_k E|F_n(k) - F(k)|, each term
+    by the normal approximation sqrt(2 F(k)(1 - F(k)) / (pi n)) of the mean
+    absolute deviation of a binomial(n, F(k)) proportion."""
+    F = np.clip(np.cumsum(np.asarray(p, dtype=np.float64), axis=-1), 0.0, 1.0)
+    return np.sqrt(2.0 * F[..., :-1] * (1.0 - F[..., :-1]) / (np.pi * n)).sum(axis=-1)

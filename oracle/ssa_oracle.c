@@ -478,12 +478,17 @@ typedef struct {
     int64_t n_traj;
     int64_t col;
     int K, N;
+    uint32_t mask;   /* stored species (bit i: species i) */
+    int outN;        /* number of stored species */
 } sink;
 
+/* Snapshot k of the stored species, in ascending species order. */
 static void write_snapshot(const sink *S, int k, const int32_t *x, uint32_t *status)
 {
+    int j = 0;
     for (int i = 0; i < S->N; ++i) {
-        int64_t idx = ((int64_t)k * S->N + i) * S->n_traj + S->col;
+        if (!((S->mask >> i) & 1u)) continue;
+        int64_t idx = ((int64_t)k * S->outN + j++) * S->n_traj + S->col;
         if (S->state_bytes == 2) {
             int32_t v = x[i];
             if (v > 32767) { v = 32767; *status |= ST_STATE_RANGE; }
@@ -670,6 +675,17 @@ static void traj_f32_mixed(const omodel *md, const runp *rp, word_stream *ws, wo
     *t_final = (double)t;
 }
 
+/* Experiment switch for the readings the paper leaves silent in uniform mode
+ * (how the random variates and the selection enter 16-bit arithmetic); 0 is
+ * the contract (reading R7).  Bits: 1 round u1 to the 16-bit type (RN) before
+ * the logarithm, as a 16-bit uniform draw would be; 2 keep u2 in binary32;
+ * 4 keep the target U2 * a0 in binary32; 8 select over binary32 partial sums
+ * (a0 and the clock still 16-bit).  Used only by the documented experiment
+ * that compares these readings with the paper's rescaled Schloegl rows. */
+static int g_uniform_variant = 0;
+
+void oracle_set_uniform_variant(int v) { g_uniform_variant = v; }
+
 static void traj_uniform(const omodel *md, const runp *rp, word_stream *ws, word_stream *wsr, int32_t *x,
                          const sink *S, uint32_t *status, int64_t *n_events, double *t_final,
                          int fmt, int sr)
@@ -710,21 +726,27 @@ static void traj_uniform(const omodel *md, const runp *rp, word_stream *ws, word
         Ssum[0] = a[0];
         for (int j = 1; j < M; ++j) Ssum[j] = rnd16(A, Ssum[j - 1] + a[j]);
         float a0 = Ssum[M - 1];
+        float Sel[OR_MAX_M];   /* the sums the selection compares (variant 8: binary32) */
+        Sel[0] = a[0];
+        for (int j = 1; j < M; ++j) Sel[j] = (g_uniform_variant & 8) ? Sel[j - 1] + a[j] : Ssum[j];
         if (f32_is_nan(a0)) { *status |= ST_NAN; break; }
         if (f32_is_inf(a0)) { *status |= ST_OVERFLOW; break; }
         if (a0 == 0.0f) break;
         uint32_t w0 = stream_word(ws, w), w1 = stream_word(ws, w + 1);
         float u1 = (float)((w0 >> 8) + 1u) * 0x1p-24f;
         float u2 = (float)(w1 >> 8) * 0x1p-24f;
+        if (g_uniform_variant & 1) u1 = rn16(fmt, u1);
         float E = rnd16(&R, -oracle_log_f32(u1));
         float U2 = rnd16(&R, u2);
+        if (g_uniform_variant & 2) U2 = u2;
         float tau = rnd16(&R, E / a0);
         float target = rnd16(&R, U2 * a0);
+        if (g_uniform_variant & 4) target = U2 * a0;
         float t_new = rnd16(A, t + tau);
         while (k < rp->K && smp[k] < t_new) write_snapshot(S, k++, x, status);
         if (t_new > t_end) break;
         int mu = -1;
-        for (int j = 0; j < M; ++j) if (Ssum[j] > target) { mu = j; break; }
+        for (int j = 0; j < M; ++j) if (Sel[j] > target) { mu = j; break; }
         if (mu < 0) for (int j = M - 1; j >= 0; --j) if (a[j] > 0.0f) { mu = j; break; }
         if (g_trace && n == g_trace_step) trace_f32(md, n, t, x, a, Ssum, u1, u2, E, U2, tau, target, t_new, mu);
         const int negative = apply_event(md, mu, x, status);
@@ -740,16 +762,18 @@ static void traj_uniform(const omodel *md, const runp *rp, word_stream *ws, word
 /* ------------------------------------------------------------------------ */
 /* Public entry: simulate trajectories g0 .. g0+n_traj-1.  Returns 0 on        */
 /* success, -1 on invalid arguments.                                           */
-/* Snapshots: out[(k*N + i)*n_traj + r] (int32 or int16 per state_bytes).     */
+/* Snapshots: out[(k*Ns + j)*n_traj + r] for the j-th stored species (bit i of  */
+/* out_species stores species i; 0 stores all), int32 or int16 per state_bytes. */
 /* ------------------------------------------------------------------------ */
 int oracle_run(int N, int M, const int32_t *order, const int32_t *stoich, const double *rate,
                const int32_t *law, const double *hill, const uint8_t *constant,
                const int32_t *x0, int64_t n_traj, uint64_t g0, double t_end,
                int K, const double *samples, int precision, int rounding, int normalise,
-               uint64_t seed, int64_t max_events, int state_bytes,
+               uint64_t seed, int64_t max_events, int state_bytes, uint32_t out_species,
                void *out, uint32_t *status, int64_t *n_events, double *t_final)
 {
     if (N < 1 || N > OR_MAX_N || M < 1 || M > OR_MAX_M || K < 0 || K > 1024) return -1;
+    if (out_species >> N) return -1;
     if (precision < 0 || precision > 5 || rounding < 0 || rounding > 2) return -1;
     if (rounding == 1 && precision < 2) return -1;
     if (rounding == 2 && precision < 4) return -1;   /* selective SR: uniform modes only */
@@ -788,6 +812,9 @@ int oracle_run(int N, int M, const int32_t *order, const int32_t *stoich, const 
         for (int i = 0; i < N; ++i) x[i] = x0[i];
         sink S;
         S.out = out; S.state_bytes = state_bytes; S.n_traj = n_traj; S.col = r; S.K = K; S.N = N;
+        S.mask = out_species ? out_species : (uint32_t)((1u << N) - 1u);
+        S.outN = 0;
+        for (int i = 0; i < N; ++i) S.outN += (int)((S.mask >> i) & 1u);
         uint32_t st = 0;
         int64_t ne = 0;
         double tf = 0.0;
@@ -1187,6 +1214,8 @@ int oracle_tau_run(int N, int M, const int32_t *order, const int32_t *stoich, co
         for (int i = 0; i < N; ++i) x[i] = x0[i];
         sink S;
         S.out = out; S.state_bytes = state_bytes; S.n_traj = n_traj; S.col = r; S.K = K; S.N = N;
+        S.mask = (uint32_t)((1u << N) - 1u);
+        S.outN = N;
         uint32_t st = 0;
         int64_t ne = 0;
         double tf = 0.0;

@@ -248,6 +248,32 @@ __global__ void hist_w1_kernel(const float *p, const float *q, int64_t rows, int
     if (lane == 0) w1[r] = acc;
 }
 
+// Expected W1 between a law p and the empirical histogram of n draws from it,
+// per row: sum_b E|F_n(b) - F(b)| with n F_n(b) binomial(n, F(b)), each term
+// by its normal approximation sqrt(2 F (1 - F) / (pi n)) (one warp per row).
+__global__ void hist_w1_noise_kernel(const float *p, int64_t rows, int bins, float n, float *out)
+{
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const float scale = 2.0f / (3.14159265358979f * n);
+    float carry = 0.0f, acc = 0.0f;
+    for (int b0 = 0; b0 < bins; b0 += 32) {
+        const int b = b0 + lane;
+        float d = b < bins ? p[r * bins + b] : 0.0f;
+        for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(0xFFFFFFFFu, d, o);
+            if (lane >= o) d += y;
+        }
+        float F = carry + d;
+        F = fminf(fmaxf(F, 0.0f), 1.0f);
+        acc += b < bins - 1 ? sqrtf(scale * F * (1.0f - F)) : 0.0f;
+        carry = __shfl_sync(0xFFFFFFFFu, carry + d, 31);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if (lane == 0) out[r] = acc;
+}
+
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Deterministic He-normal initialisation on the host (splitmix64 + Box-Muller).
@@ -714,6 +740,14 @@ int ssa_histogram(const int32_t *counts, int64_t n_sets, int64_t traj_per_set, i
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     histogram_kernel<<<(unsigned)n_sets, 256, (size_t)bins * sizeof(unsigned int), st>>>(counts, traj_per_set, bins,
                                                                                           hist);
+    return cudaGetLastError() == cudaSuccess ? SSA_OK : SSA_ECUDA;
+}
+
+int ssa_hist_w1_noise(const float *p, int64_t rows, int bins, double n_draws, float *out, void *stream)
+{
+    if (!p || !out || rows < 1 || bins < 1 || !(n_draws >= 1.0)) return SSA_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    hist_w1_noise_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(p, rows, bins, (float)n_draws, out);
     return cudaGetLastError() == cudaSuccess ? SSA_OK : SSA_ECUDA;
 }
 

@@ -6,6 +6,7 @@
 // data runs in the CUDA kernels; this file only marshals.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -161,6 +162,31 @@ void rate_constants(const ssa_model &m, const int32_t *x0, int normalise, double
     }
 }
 
+// Rough events per trajectory, a0(x0) * t_end in binary64: the scale of the
+// work a run does per trajectory (used only to pick how host outputs are
+// delivered; the order of magnitude is what matters).
+double estimated_events(const ssa_model &m, const int32_t *x0, int normalise, double t_end)
+{
+    double c[ssa::kMaxM];
+    int8_t folded[ssa::kMaxM][ssa::kMaxN];
+    rate_constants(m, x0, normalise, c, folded);
+    double a0 = 0.0;
+    for (int j = 0; j < m.M; ++j) {
+        if (m.law[j] == SSA_LAW_HILL_REPRESSION) {
+            const double P = (double)x0[(int)m.hill[j][3]];
+            a0 += m.hill[j][0] + m.hill[j][1] / (1.0 + std::pow(P, m.hill[j][2]));
+            continue;
+        }
+        double a = c[j];
+        for (int i = 0; i < m.N; ++i) {
+            if (folded[j][i]) continue;
+            for (int q = 0; q < m.order[j][i]; ++q) a *= (double)(x0[i] - q > 0 ? x0[i] - q : 0);
+        }
+        a0 += a;
+    }
+    return a0 * t_end;
+}
+
 int chain_ops(const ssa_model &m, int j, int8_t folded[][ssa::kMaxN])
 {
     if (m.law[j] == SSA_LAW_HILL_REPRESSION) return (int)m.hill[j][2] + 3;
@@ -172,7 +198,7 @@ int chain_ops(const ssa_model &m, int j, int8_t folded[][ssa::kMaxN])
 
 int validate_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, const int32_t *x0, double t_end,
                  int n_samples, const double *sample_times, int precision, int rounding, int64_t max_events,
-                 int state_bytes)
+                 int state_bytes, uint32_t out_species = 0)
 {
     if (!model) return fail(SSA_EINVAL, "model is NULL");
     if (n_traj < 0) return fail(SSA_EINVAL, "n_traj must be >= 0");
@@ -196,7 +222,15 @@ int validate_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, c
         return fail(SSA_EINVAL, "selective stochastic rounding needs a uniform 16-bit mode");
     if (max_events < 0) return fail(SSA_EINVAL, "max_events must be >= 0");
     if (state_bytes != 2 && state_bytes != 4) return fail(SSA_EINVAL, "state_bytes must be 2 or 4");
+    if (model->N < 32 && (out_species >> model->N) != 0u)
+        return fail(SSA_EINVAL, "out_species names species beyond n_species = %d", model->N);
     return SSA_OK;
+}
+
+// Stored species of a run: the caller's mask, 0 meaning all.
+uint32_t out_mask_of(const ssa_model &m, uint32_t out_species)
+{
+    return out_species ? out_species : ((1u << m.N) - 1u);
 }
 
 // Fill the kernel arguments common to single and batched runs.
@@ -204,6 +238,8 @@ void fill_structure(const ssa_model &m, int normalise, const int32_t *x0, ssa::R
 {
     a.N = m.N;
     a.M = m.M;
+    a.out_mask = (m.N >= 32) ? 0xFFFFFFFFu : ((1u << m.N) - 1u);   // every species stored
+    a.out_N = m.N;
     rate_constants(m, x0, normalise, a.cprime, a.folded);
     int start = 0;
     for (int j = 0; j < m.M; ++j) {
@@ -229,8 +265,8 @@ void fill_structure(const ssa_model &m, int normalise, const int32_t *x0, ssa::R
 // Arguments are validated by the caller.
 int launch_run(const ssa_model *model, int64_t n_work, int64_t stride, uint64_t traj_offset, const int32_t *x0,
                double t_end, int n_samples, const double *sample_times, int precision, int rounding, int normalise,
-               uint64_t seed, int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
-               int64_t *n_events, double *t_final, cudaStream_t s)
+               uint64_t seed, int64_t max_events, int state_bytes, uint32_t out_species, void *out,
+               uint32_t *traj_status, int64_t *n_events, double *t_final, cudaStream_t s)
 {
     ssa::RunArgs *a = new (std::nothrow) ssa::RunArgs;
     if (!a) return fail(SSA_ENOMEM, "out of host memory");
@@ -250,6 +286,8 @@ int launch_run(const ssa_model *model, int64_t n_work, int64_t stride, uint64_t 
     a->max_events = max_events;
     a->out = out;
     a->state_bytes = state_bytes;
+    a->out_mask = out_mask_of(*model, out_species);
+    a->out_N = __builtin_popcount(a->out_mask);
     a->status = traj_status;
     a->n_events = n_events;
     a->t_final = t_final;
@@ -391,16 +429,16 @@ int ssa_model_kernel_family(const ssa_model *model) { return model ? model->fami
 
 int ssa_ensemble_run(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, const int32_t *x0, double t_end,
                      int n_samples, const double *sample_times, int precision, int rounding, int normalise,
-                     uint64_t seed, int64_t max_events, int state_bytes, void *out, uint32_t *traj_status,
-                     int64_t *n_events, double *t_final, void *stream)
+                     uint64_t seed, int64_t max_events, int state_bytes, uint32_t out_species, void *out,
+                     uint32_t *traj_status, int64_t *n_events, double *t_final, void *stream)
 {
     int rc = validate_run(model, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
-                          max_events, state_bytes);
+                          max_events, state_bytes, out_species);
     if (rc != SSA_OK) return rc;
     if (n_traj > 0 && (!out || !traj_status)) return fail(SSA_EINVAL, "out and traj_status are required");
     if (n_traj == 0) return SSA_OK;
     return launch_run(model, n_traj, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
-                      normalise, seed, max_events, state_bytes, out, traj_status, n_events, t_final,
+                      normalise, seed, max_events, state_bytes, out_species, out, traj_status, n_events, t_final,
                       static_cast<cudaStream_t>(stream));
 }
 
@@ -468,27 +506,35 @@ extern "C" {
 
 int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_offset, const int32_t *x0,
                           double t_end, int n_samples, const double *sample_times, int precision, int rounding,
-                          int normalise, uint64_t seed, int64_t max_events, int state_bytes, void *out,
-                          uint32_t *traj_status, int64_t *n_events, double *t_final, void *stream)
+                          int normalise, uint64_t seed, int64_t max_events, int state_bytes, uint32_t out_species,
+                          void *out, uint32_t *traj_status, int64_t *n_events, double *t_final, void *stream)
 {
     int rc = validate_run(model, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
-                          max_events, state_bytes);
+                          max_events, state_bytes, out_species);
     if (rc != SSA_OK) return rc;
     if (n_traj > 0 && (!out || !traj_status)) return fail(SSA_EINVAL, "out and traj_status are required");
     if (n_traj == 0) return SSA_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t out_N = (size_t)__builtin_popcount(out_mask_of(*model, out_species));
+    const size_t out_bytes = (size_t)n_samples * out_N * (size_t)n_traj * (size_t)state_bytes;
     // Page-locked outputs: the kernel writes the results straight into them
     // while it runs (over NVLink-C2C on Grace-Blackwell), with no staging
-    // buffers and no copy after the kernel.
-    if (pinned_for_device(out) && pinned_for_device(traj_status) && (!n_events || pinned_for_device(n_events)) &&
-        (!t_final || pinned_for_device(t_final))) {
+    // buffers and no copy after the kernel -- when the snapshot stream is
+    // sparse.  Each snapshot store crosses the link on its own, so a dense
+    // stream (more than kDirectBytesPerEvent snapshot bytes per estimated
+    // event) goes through device staging and one bulk copy instead.
+    constexpr double kDirectBytesPerEvent = 0.05;
+    const double bytes_per_event = (double)(out_bytes / (size_t)n_traj) /
+                                   std::max(1.0, estimated_events(*model, x0, normalise, t_end));
+    if (bytes_per_event <= kDirectBytesPerEvent && pinned_for_device(out) && pinned_for_device(traj_status) &&
+        (!n_events || pinned_for_device(n_events)) && (!t_final || pinned_for_device(t_final))) {
         rc = launch_run(model, n_traj, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
-                        normalise, seed, max_events, state_bytes, out, traj_status, n_events, t_final, s);
+                        normalise, seed, max_events, state_bytes, out_species, out, traj_status, n_events, t_final,
+                        s);
         const cudaError_t es = cudaStreamSynchronize(s);
         if (rc == SSA_OK && es != cudaSuccess) rc = cuda_fail(es, "cudaStreamSynchronize");
         return rc;
     }
-    const size_t out_bytes = (size_t)n_samples * (size_t)model->N * (size_t)n_traj * (size_t)state_bytes;
     const size_t st_bytes = (size_t)n_traj * sizeof(uint32_t);
     const size_t ev_bytes = n_events ? (size_t)n_traj * sizeof(int64_t) : 0;
     const size_t tf_bytes = t_final ? (size_t)n_traj * sizeof(double) : 0;
@@ -506,7 +552,7 @@ int ssa_ensemble_run_host(const ssa_model *model, int64_t n_traj, uint64_t traj_
     uint32_t *d_st = reinterpret_cast<uint32_t *>(p); p += st_bytes;
     void *d_out = p;
     rc = launch_run(model, n_traj, n_traj, traj_offset, x0, t_end, n_samples, sample_times, precision, rounding,
-                    normalise, seed, max_events, state_bytes, d_out, d_st, d_ev, d_tf, s);
+                    normalise, seed, max_events, state_bytes, out_species, d_out, d_st, d_ev, d_tf, s);
     if (rc == SSA_OK) {
         e = cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(traj_status, d_st, st_bytes, cudaMemcpyDeviceToHost, s);

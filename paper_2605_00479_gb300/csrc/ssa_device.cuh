@@ -90,8 +90,10 @@ struct RunArgs {
     uint32_t key0, key1;
     int64_t max_events;
     // outputs
-    void *out;                         // [K][N][n_traj] int32 or int16
+    void *out;                         // [K][out_N][n_traj] int32 or int16
     int state_bytes;
+    uint32_t out_mask;                 // bit i: species i is stored (ascending order)
+    int out_N;                         // stored species (popcount of out_mask)
     uint32_t *status;
     int64_t *n_events;
     double *t_final;
@@ -461,8 +463,9 @@ __device__ __forceinline__ void store_state(const RunArgs &a, int k, int64_t ite
     const int64_t stride = a.n_traj;
     unroll<Model::N>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        if (i < a.N) {
-            const int64_t idx = ((int64_t)k * a.N + i) * stride + col;
+        if (i < a.N && ((a.out_mask >> i) & 1u)) {
+            const int j = __popc(a.out_mask & ((1u << i) - 1u));   // position among the stored species
+            const int64_t idx = ((int64_t)k * a.out_N + j) * stride + col;
             int v = x[i];
             if (a.state_bytes == 2) {
                 if (v > 32767) { v = 32767; status |= ST_STATE_RANGE; }

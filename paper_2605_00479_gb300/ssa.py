@@ -24,7 +24,7 @@ FAMILIES = {0: "general", 1: "birth_death", 2: "schlogl", 3: "telegraph", 4: "di
 # name -> (restype, argtypes) for every function declared in include/ssa.h
 _P = ctypes.c_void_p
 _I, _I64, _U64, _D = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
-_RUN_ARGS = [_P, _I64, _U64, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, _P, _P, _P, _P, _P]
+_RUN_ARGS = [_P, _I64, _U64, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, ctypes.c_uint32, _P, _P, _P, _P, _P]
 SIGNATURES = {
     "ssa_model_create": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "ssa_model_destroy": (None, [_P]),
@@ -65,6 +65,7 @@ SIGNATURES = {
     "ssa_round16": (_I, [_P, _P, _I64, _I, _I, _I, _P, _P]),
     "ssa_histogram": (_I, [_P, _I64, _I64, _I, _P, _P]),
     "ssa_hist_w1": (_I, [_P, _P, _I64, _I, _P, _P]),
+    "ssa_hist_w1_noise": (_I, [_P, _I64, _I, _D, _P, _P]),
     "ssa_count_histogram": (_I, [_P, _I, _I64, _I, _P, _P, _P]),
     "ssa_hist_ks_w1": (_I, [_P, _P, _I, _P, _P]),
     "ssa_dwell_histogram": (_I, [_P, _I, _I, _I64, _I64, _P, _P]),
@@ -183,21 +184,28 @@ def _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision,
     return x0, st, prec, rnd
 
 
+def _stored(model, out_species):
+    """Number of stored species for an out_species mask (0: all)."""
+    return model.N if not out_species else bin(int(out_species)).count("1")
+
+
 def ensemble_run(model, n_traj, x0, t_end, sample_times, precision="fp64", rounding="rn", normalise=False, seed=0,
                  max_events=10**9, state_bytes=4, out=None, status=None, n_events=None, t_final=None,
-                 stream=None, traj_offset=0, with_events=True, with_t_final=True):
+                 stream=None, traj_offset=0, with_events=True, with_t_final=True, out_species=0):
     """Launch ssa_ensemble_run on CUDA tensors (allocated here when None).
 
-    Returns a dict of device tensors: snapshots [K, N, n_traj], status,
-    n_events, t_final.  Asynchronous on ``stream`` (a torch.cuda.Stream or
-    None for the current stream)."""
+    Returns a dict of device tensors: snapshots [K, Ns, n_traj] (Ns species
+    stored per the out_species mask, 0 = all), status, n_events, t_final.
+    Asynchronous on ``stream`` (a torch.cuda.Stream or None for the current
+    stream)."""
     import torch
     x0, st, prec, rnd = _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision, rounding,
                                      normalise, seed, max_events, state_bytes)
     dev = torch.device("cuda", torch.cuda.current_device())
     K = st.size
     if out is None:
-        out = torch.empty((K, model.N, n_traj), dtype=torch.int16 if state_bytes == 2 else torch.int32, device=dev)
+        out = torch.empty((K, _stored(model, out_species), n_traj), dtype=torch.int16 if state_bytes == 2
+                          else torch.int32, device=dev)
     if status is None:
         status = torch.empty(n_traj, dtype=torch.int32, device=dev)
     if n_events is None and with_events:
@@ -207,20 +215,21 @@ def ensemble_run(model, n_traj, x0, t_end, sample_times, precision="fp64", round
     s = stream if stream is not None else torch.cuda.current_stream()
     _check(lib().ssa_ensemble_run(model.handle, int(n_traj), int(traj_offset), _np_ptr(x0), float(t_end), K,
                                   _np_ptr(st), prec, rnd, int(bool(normalise)), int(seed) & (2**64 - 1),
-                                  int(max_events), int(state_bytes), _dev_ptr(out), _dev_ptr(status),
-                                  _dev_ptr(n_events), _dev_ptr(t_final), ctypes.c_void_p(s.cuda_stream)))
+                                  int(max_events), int(state_bytes), int(out_species), _dev_ptr(out),
+                                  _dev_ptr(status), _dev_ptr(n_events), _dev_ptr(t_final),
+                                  ctypes.c_void_p(s.cuda_stream)))
     return {"snapshots": out, "status": status, "n_events": n_events, "t_final": t_final}
 
 
 def ensemble_run_host(model, n_traj, x0, t_end, sample_times, precision="fp64", rounding="rn", normalise=False,
                       seed=0, max_events=10**9, state_bytes=4, out=None, status=None, n_events=None, t_final=None,
-                      stream=None, traj_offset=0):
+                      stream=None, traj_offset=0, out_species=0):
     """ssa_ensemble_run_host: host (numpy) outputs; synchronous."""
     x0, st, prec, rnd = _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision, rounding,
                                      normalise, seed, max_events, state_bytes)
     K = st.size
     if out is None:
-        out = np.empty((K, model.N, n_traj), dtype=np.int16 if state_bytes == 2 else np.int32)
+        out = np.empty((K, _stored(model, out_species), n_traj), dtype=np.int16 if state_bytes == 2 else np.int32)
     if status is None:
         status = np.empty(n_traj, dtype=np.uint32)
     if n_events is None:
@@ -232,8 +241,8 @@ def ensemble_run_host(model, n_traj, x0, t_end, sample_times, precision="fp64", 
         sp = ctypes.c_void_p(stream.cuda_stream)
     _check(lib().ssa_ensemble_run_host(model.handle, int(n_traj), int(traj_offset), _np_ptr(x0), float(t_end), K,
                                        _np_ptr(st), prec, rnd, int(bool(normalise)), int(seed) & (2**64 - 1),
-                                       int(max_events), int(state_bytes), _np_ptr(out), _np_ptr(status),
-                                       _np_ptr(n_events), _np_ptr(t_final), sp))
+                                       int(max_events), int(state_bytes), int(out_species), _np_ptr(out),
+                                       _np_ptr(status), _np_ptr(n_events), _np_ptr(t_final), sp))
     return {"snapshots": out, "status": status, "n_events": n_events, "t_final": t_final}
 
 
@@ -249,7 +258,8 @@ def tau_run(model, n_traj, x0, t_end, tau, sample_times, precision="fp64", round
     dev = torch.device("cuda", torch.cuda.current_device())
     K = st.size
     if out is None:
-        out = torch.empty((K, model.N, n_traj), dtype=torch.int16 if state_bytes == 2 else torch.int32, device=dev)
+        out = torch.empty((K, _stored(model, out_species), n_traj), dtype=torch.int16 if state_bytes == 2
+                          else torch.int32, device=dev)
     if status is None:
         status = torch.empty(n_traj, dtype=torch.int32, device=dev)
     if n_events is None:
@@ -485,6 +495,16 @@ def hist_w1(p, q, out=None, stream=None):
 
 
 # ------------------------------------------------------- ensemble statistics
+
+def hist_w1_noise(p, n_draws, out=None, stream=None):
+    """Expected W1 sampling noise of an n-draw histogram of each row's law."""
+    import torch
+    if out is None:
+        out = torch.empty(p.shape[0], dtype=torch.float32, device=p.device)
+    _check(lib().ssa_hist_w1_noise(_dev_ptr(p), int(p.shape[0]), int(p.shape[1]), float(n_draws), _dev_ptr(out),
+                                   _stream_ptr(stream)))
+    return out
+
 
 def count_histogram(values, bins, hist=None, clamped=None, stream=None):
     """ssa_count_histogram on a contiguous int32/int16 CUDA tensor; returns

@@ -375,6 +375,20 @@ def test_histogram_and_w1_kernels(ssa):
     np.testing.assert_allclose(w.cpu().numpy(), mlp.wasserstein_hist(ref, q), rtol=1e-4, atol=1e-5)
 
 
+def test_w1_noise_kernel_matches_oracle(ssa):
+    """ssa_hist_w1_noise against the oracle's expected_w1_noise (fp32 prefix
+    sums and square roots vs float64: 1e-4 relative)."""
+    from oracle import mlp
+    rng = np.random.default_rng(8)
+    p = rng.random((300, 128)) ** 4
+    p[:5, 40:] = 0.0                              # laws with empty tails
+    p /= p.sum(axis=1, keepdims=True)
+    for n in (64, 1000):
+        got = ssa.hist_w1_noise(torch.from_numpy(p.astype(np.float32)).cuda(), n).cpu().numpy()
+        np.testing.assert_allclose(got, mlp.expected_w1_noise(p.astype(np.float32).astype(np.float64), n),
+                                   rtol=1e-4, atol=1e-6)
+
+
 def test_graph_driven_training_matches_step_by_step(ssa):
     """ssa_surrogate_train (one captured step replayed) against the same steps
     issued one by one through ssa_surrogate_train_step with the documented

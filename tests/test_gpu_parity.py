@@ -177,36 +177,46 @@ def test_large_host_entry_point_matches_device(ssa, state_bytes):
     assert_same({**h, "status": h["status"].view(np.int32)}, {**g, "status": g["status"].view(np.uint32)})
 
 
+@pytest.mark.parametrize("stream_kind", ["sparse", "dense"])
 @pytest.mark.parametrize("pinned", ["all", "all_but_status", "no_optional"])
-def test_host_entry_point_page_locked_outputs(ssa, pinned):
-    """Page-locked outputs take the direct-write path (the kernel writes into
-    host memory); a pageable buffer among them sends the call through device
-    staging.  Results equal the device entry point either way."""
-    tel = P.telegraph(0.5, 0.5, 20.0, 1.0)
-    m = ssa.Model.from_dict(tel)
-    n, off = 200003, 777
-    samples = P.even_samples(5.0, 6)
+def test_host_entry_point_page_locked_outputs(ssa, pinned, stream_kind):
+    """Page-locked outputs with a sparse snapshot stream take the direct-write
+    path (the kernel writes into host memory: Schloegl, X stored, ~10^4
+    events per trajectory); a dense stream (telegraph, every species at 6
+    times over a few events) or a pageable buffer among the outputs goes
+    through device staging.  Results equal the device entry point either way."""
+    if stream_kind == "sparse":
+        md = P.schlogl()
+        x0, t_end, mask, norm, n, prec = P.schlogl_x0(md), 5.0, 0b001, True, 20011, "mixed_bf16"
+    else:
+        md = P.telegraph(0.5, 0.5, 20.0, 1.0)
+        x0, t_end, mask, norm, n, prec = P.TELEGRAPH_X0, 5.0, 0, False, 200003, "mixed_bf16"
+    m = ssa.Model.from_dict(md)
+    off = 777
+    samples = P.even_samples(t_end, 6)
     K = len(samples)
-    out = torch.full((K, m.N, n), -5, dtype=torch.int32).pin_memory()
+    Ns = m.N if not mask else bin(mask).count("1")
+    out = torch.full((K, Ns, n), -5, dtype=torch.int32).pin_memory()
     st = torch.full((n,), -5, dtype=torch.int32)
     st = st.pin_memory() if pinned != "all_but_status" else st
     ev = torch.full((n,), -5, dtype=torch.int64).pin_memory() if pinned != "no_optional" else None
     tf = torch.full((n,), -5.0, dtype=torch.float64).pin_memory() if pinned != "no_optional" else None
     import ctypes
     vp = ctypes.c_void_p
-    x0 = np.ascontiguousarray(P.TELEGRAPH_X0, dtype=np.int32)
+    x0 = np.ascontiguousarray(x0, dtype=np.int32)
     smp = np.ascontiguousarray(samples, dtype=np.float64)
     rc = ssa.lib().ssa_ensemble_run_host(
-        m.handle, n, off, x0.ctypes.data_as(vp), 5.0, K, smp.ctypes.data_as(vp), ssa.PRECISION["mixed_bf16"],
-        ssa.ROUNDING["sr"], 0, 13, 10**5, 4, vp(out.data_ptr()), vp(st.data_ptr()),
+        m.handle, n, off, x0.ctypes.data_as(vp), t_end, K, smp.ctypes.data_as(vp), ssa.PRECISION[prec],
+        ssa.ROUNDING["sr"], int(norm), 13, 10**5, 4, mask, vp(out.data_ptr()), vp(st.data_ptr()),
         None if ev is None else vp(ev.data_ptr()), None if tf is None else vp(tf.data_ptr()), None)
     assert rc == 0, ssa.lib().ssa_last_error()
-    g, _ = gpu_run(ssa, tel, P.TELEGRAPH_X0, n, 5.0, samples, "mixed_bf16", "sr", False, 13, 10**5, traj_offset=off)
-    np.testing.assert_array_equal(out.numpy(), g["snapshots"])
-    np.testing.assert_array_equal(st.numpy(), g["status"])
+    r = ssa.ensemble_run(m, n, x0, t_end, samples, prec, "sr", norm, 13, 10**5, traj_offset=off, out_species=mask)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.numpy(), r["snapshots"].cpu().numpy())
+    np.testing.assert_array_equal(st.numpy(), r["status"].cpu().numpy())
     if ev is not None:
-        np.testing.assert_array_equal(ev.numpy(), g["n_events"])
-        np.testing.assert_array_equal(tf.numpy().view(np.uint64), g["t_final"].view(np.uint64))
+        np.testing.assert_array_equal(ev.numpy(), r["n_events"].cpu().numpy())
+        np.testing.assert_array_equal(tf.numpy().view(np.uint64), r["t_final"].cpu().numpy().view(np.uint64))
 
 
 BENCH_MODES = [("mixed_f16", "rn"), ("mixed_bf16", "rn"), ("uniform_f16", "rn"), ("uniform_f16", "sr"),
@@ -237,3 +247,30 @@ def test_full_size_schlogl_sampled_trajectories(ssa, prec, rnd):
     if rnd != "rn" or prec.startswith("mixed"):
         xs = g["snapshots"][-1, 0]
         assert np.mean(xs < 250) > 0.2 and np.mean(xs > 400) > 0.1
+
+
+@pytest.mark.parametrize("mask,sb", [(0b001, 2), (0b101, 4), (0b110, 2)])
+def test_species_mask_matches_oracle(ssa, mask, sb):
+    """Snapshots of a subset of species (out_species): the Schloegl reservoirs
+    left out, or stored beside X; int16 storage clamps (and flags) stored
+    species only.  Device and host entry points against the oracle."""
+    m = P.schlogl()
+    x0 = P.schlogl_x0(m)
+    smp = P.even_samples(2.0, 6)
+    o = oracle.run(m, x0, 1500, 2.0, smp, "uniform_f16", "sr", True, 21, 10**6, state_bytes=sb, out_species=mask)
+    model = ssa.Model.from_dict(m)
+    g = ssa.ensemble_run(model, 1500, x0, 2.0, smp, "uniform_f16", "sr", True, 21, 10**6, sb, out_species=mask)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(g["snapshots"].cpu().numpy(), o["snapshots"])
+    np.testing.assert_array_equal(g["status"].cpu().numpy().view(np.uint32), o["status"])
+    np.testing.assert_array_equal(g["n_events"].cpu().numpy(), o["n_events"])
+    h = ssa.ensemble_run_host(model, 1500, x0, 2.0, smp, "uniform_f16", "sr", True, 21, 10**6, sb, out_species=mask)
+    np.testing.assert_array_equal(h["snapshots"], o["snapshots"])
+    np.testing.assert_array_equal(h["status"], o["status"])
+
+
+def test_species_mask_rejects_unknown_species(ssa):
+    m = ssa.Model.from_dict(P.schlogl())
+    with pytest.raises(ssa.SSAError):
+        ssa.ensemble_run(m, 10, P.schlogl_x0(P.schlogl()), 1.0, [1.0], "fp64", "rn", True, 1, 100, 4,
+                         out=torch.zeros((1, 1, 10), dtype=torch.int32, device="cuda"), out_species=0b1000)

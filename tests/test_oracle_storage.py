@@ -47,3 +47,27 @@ def test_rdme_int16_storage_is_output_only():
     clamped = _check_storage(a, b, 3)
     assert clamped.all()
     assert a["snapshots"][0].min() > 10000 and a["snapshots"][1].min() > 32767
+
+
+def test_species_mask_stores_a_subset_and_clamps_only_stored_species():
+    """out_species: the snapshots hold the chosen species in ascending order,
+    identical to the full output's rows; the trajectories are unchanged; the
+    int16 clamp flag comes only from stored species (the Schloegl reservoirs
+    A = 1e5, B = 2e5 clamp when stored, not when left out)."""
+    m = P.schlogl()
+    x0 = P.schlogl_x0(m)
+    smp = P.even_samples(1.0, 4)
+    full = oracle.run(m, x0, 40, 1.0, smp, "mixed_f16", "sr", True, 3, 10**6, state_bytes=2)
+    only_x = oracle.run(m, x0, 40, 1.0, smp, "mixed_f16", "sr", True, 3, 10**6, state_bytes=2, out_species=0b001)
+    assert only_x["snapshots"].shape == (4, 1, 40)
+    np.testing.assert_array_equal(only_x["snapshots"][:, 0], full["snapshots"][:, 0])
+    np.testing.assert_array_equal(only_x["n_events"], full["n_events"])
+    np.testing.assert_array_equal(only_x["t_final"], full["t_final"])
+    assert np.all(full["status"] & oracle.STATUS_STATE_RANGE)
+    assert not np.any(only_x["status"] & oracle.STATUS_STATE_RANGE)
+    xb = oracle.run(m, x0, 40, 1.0, smp, "mixed_f16", "sr", True, 3, 10**6, state_bytes=4, out_species=0b101)
+    full4 = oracle.run(m, x0, 40, 1.0, smp, "mixed_f16", "sr", True, 3, 10**6, state_bytes=4)
+    np.testing.assert_array_equal(xb["snapshots"], full4["snapshots"][:, [0, 2]])
+    import pytest
+    with pytest.raises(ValueError):
+        oracle.run(m, x0, 4, 1.0, smp, "fp64", "rn", True, 3, 10**6, out_species=0b1000)

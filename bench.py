@@ -107,16 +107,14 @@ def ops_per_event(prec, rnd):
 
 
 # ------------------------------------------------------------ ncu traffic
-# DRAM bytes (read + write) per trajectory of the step's kernels, from one ncu
-# capture (the uniform_f16 RN kernel profile; a 3e5-trajectory launch scaled
-# per trajectory: the traffic is the snapshot stream, proportional to the
-# trajectories).  Valid only for the kernel source it was measured on: the
+# DRAM bytes (read + write) per trajectory of the headline kernel, from one
+# ncu count of a 3e5-trajectory launch scaled per trajectory (the traffic is
+# the snapshot stream, proportional to the trajectories).  Valid only for the kernel source it was measured on: the
 # key includes a hash of the device code, and a changed kernel reports null.
 NCU_TRAFFIC_PER_TRAJ = {
-    # uniform_f16 RN, 3e5 trajectories, default launch shape (256 threads chosen for this
-    # kernel, 32 step pairs per refill check, tail compaction): 269,713,408 B read +
-    # 438,277,376 B written
-    ("9411da1654565aeb", "uniform_f16:rn"): (269713408 + 438277376) / 300000,
+    # mixed_bf16 RN (the headline kernel), 3e5 trajectories, snapshots of X only,
+    # default launch shape: 39,560,448 B read + 50,652,672 B written
+    ("9da781fe6abee25b", "mixed_bf16:rn"): (39560448 + 50652672) / 300000,
 }
 
 

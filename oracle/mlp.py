@@ -176,5 +176,7 @@ def expected_w1_noise(p, n):
     empirical histogram of n draws from it: sum_k E|F_n(k) - F(k)|, each term
     by the normal approximation sqrt(2 F(k)(1 - F(k)) / (pi n)) of the mean
     absolute deviation of a binomial(n, F(k)) proportion."""
-    F = np.clip(np.cumsum(np.asarray(p, dtype=np.float64), axis=-1), 0.0, 1.0)
-    return np.sqrt(2.0 * F[..., :-1] * (1.0 - F[..., :-1]) / (np.pi * n)).sum(axis=-1)
+    p = np.asarray(p, dtype=np.float64)
+    F = np.cumsum(p, axis=-1)
+    rest = np.maximum(F[..., -1:] - F, 0.0)          # 1 - F as the remaining mass
+    return np.sqrt(2.0 * np.maximum(F[..., :-1], 0.0) * rest[..., :-1] / (np.pi * n)).sum(axis=-1)

@@ -251,24 +251,33 @@ __global__ void hist_w1_kernel(const float *p, const float *q, int64_t rows, int
 // Expected W1 between a law p and the empirical histogram of n draws from it,
 // per row: sum_b E|F_n(b) - F(b)| with n F_n(b) binomial(n, F(b)), each term
 // by its normal approximation sqrt(2 F (1 - F) / (pi n)) (one warp per row).
+// 1 - F is taken as the remaining mass T - F (T the row total, summed in the
+// same order), so bins past the last nonzero probability contribute exactly 0.
 __global__ void hist_w1_noise_kernel(const float *p, int64_t rows, int bins, float n, float *out)
 {
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
     const float scale = 2.0f / (3.14159265358979f * n);
-    float carry = 0.0f, acc = 0.0f;
-    for (int b0 = 0; b0 < bins; b0 += 32) {
+    // inclusive prefix sums of the row, 32 bins at a time
+    auto prefix = [&](int b0, float carry) {
         const int b = b0 + lane;
         float d = b < bins ? p[r * bins + b] : 0.0f;
         for (int o = 1; o < 32; o <<= 1) {
             const float y = __shfl_up_sync(0xFFFFFFFFu, d, o);
             if (lane >= o) d += y;
         }
-        float F = carry + d;
-        F = fminf(fmaxf(F, 0.0f), 1.0f);
-        acc += b < bins - 1 ? sqrtf(scale * F * (1.0f - F)) : 0.0f;
-        carry = __shfl_sync(0xFFFFFFFFu, carry + d, 31);
+        return carry + d;
+    };
+    float total = 0.0f;
+    for (int b0 = 0; b0 < bins; b0 += 32) total = __shfl_sync(0xFFFFFFFFu, prefix(b0, total), 31);
+    float carry = 0.0f, acc = 0.0f;
+    for (int b0 = 0; b0 < bins; b0 += 32) {
+        const int b = b0 + lane;
+        const float F = prefix(b0, carry);
+        const float rest = fmaxf(total - F, 0.0f);
+        acc += b < bins - 1 ? sqrtf(scale * fmaxf(F, 0.0f) * rest) : 0.0f;
+        carry = __shfl_sync(0xFFFFFFFFu, F, 31);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     if (lane == 0) out[r] = acc;

@@ -143,11 +143,9 @@ __device__ __forceinline__ void store_packed16(uint8_t *base, int64_t r, int c0,
 __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ GemmArgs g)
 {
     extern __shared__ uint8_t dyn_smem[];
-    __shared__ uint64_t bars[2];
+    __shared__ uint64_t bars[4];          // operands landed in stage 0 / 1, MMAs reading stage 0 / 1 done
     __shared__ uint32_t tmem_base_s;
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_smem) + 127) & ~uintptr_t(127));
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + (size_t)kTileM * g.kchunk * 2;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x;
@@ -155,8 +153,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
     const uint32_t ncols = nt <= 32 ? 32u : (nt <= 64 ? 64u : (nt <= 128 ? 128u : 256u));
     if (warp == 0) tmem_alloc(&tmem_base_s, ncols);
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int b = 0; b < 4; ++b) mbar_init(&bars[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -169,51 +166,75 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
     const uint32_t rg_bytes = (uint32_t)g.kchunk * 16u;   // one 8-row group of one stage
     const uint32_t stage_bytes = (uint32_t)(kTileM + nt) * (uint32_t)g.kchunk * 2u;
     const uint32_t limit = g.spin_limit ? g.spin_limit : kSpinLimit;
-    int err = ERR_NONE;
-    bool loads_pending = false, mma_pending = false;   // issued work whose completion was not seen
-    int ch = 0;
-    for (; ch < n_chunks; ++ch) {
-        const uint32_t parity = (uint32_t)(ch & 1);
-        if (warp == 0 && g.withhold != 1) {
-            if (lane == 0) mbar_expect_tx(&bars[0], stage_bytes);
-            __syncwarp();
-            const int colA = g.a_col0 + ch * g.kchunk, colB = g.b_col0 + ch * g.kchunk;
-            const int groups = kTileM / 8 + nt / 8;
-            for (int q = lane; q < groups; q += 32) {
-                if (q < kTileM / 8) {
-                    const int64_t rg = (int64_t)tile * (kTileM / 8) + q;
-                    bulk_g2s(sA + (size_t)q * rg_bytes, g.A + (rg * (g.lda_cols / 8) + colA / 8) * 128, rg_bytes, &bars[0]);
-                } else {
-                    const int64_t rg = q - kTileM / 8;
-                    const int64_t brg = (int64_t)(n0 / 8) + rg;
-                    bulk_g2s(sB + (size_t)rg * rg_bytes, g.B + (brg * (g.ldb_cols / 8) + colB / 8) * 128, rg_bytes,
-                             &bars[0]);
-                }
+
+    // With two stages (g.stages, set when the reduction has several chunks and
+    // both fit in shared memory) the copies of chunk c + 1 land while the MMAs
+    // of chunk c run.  Stage c % stages holds chunk c; its barriers complete
+    // once per use, so chunk c waits for parity (c / stages) & 1.
+    const int stages = g.stages == 2 ? 2 : 1;
+    auto stage_a = [&](int st) { return smem + (size_t)st * stage_bytes; };
+    auto issue_load = [&](int c) {   // warp 0, all lanes
+        const int st = c % stages;
+        uint8_t *sA = stage_a(st), *sB = sA + (size_t)kTileM * g.kchunk * 2;
+        if (lane == 0) mbar_expect_tx(&bars[st], stage_bytes);
+        __syncwarp();
+        const int colA = g.a_col0 + c * g.kchunk, colB = g.b_col0 + c * g.kchunk;
+        const int groups = kTileM / 8 + nt / 8;
+        for (int q = lane; q < groups; q += 32) {
+            if (q < kTileM / 8) {
+                const int64_t rg = (int64_t)tile * (kTileM / 8) + q;
+                bulk_g2s(sA + (size_t)q * rg_bytes, g.A + (rg * (g.lda_cols / 8) + colA / 8) * 128, rg_bytes,
+                         &bars[st]);
+            } else {
+                const int64_t rg = q - kTileM / 8;
+                const int64_t brg = (int64_t)(n0 / 8) + rg;
+                bulk_g2s(sB + (size_t)rg * rg_bytes, g.B + (brg * (g.ldb_cols / 8) + colB / 8) * 128, rg_bytes,
+                         &bars[st]);
             }
         }
-        loads_pending = g.withhold != 1;
-        if (!__syncthreads_and(mbar_wait(&bars[0], parity, limit))) {
+    };
+    // issued work whose completion has not been observed (the same in every
+    // thread): the chunk loading into each stage, the last chunk committed
+    int pend_load[2] = {-1, -1};
+    int pend_mma = -1;
+    int err = ERR_NONE;
+    for (int c = 0; c < stages && c < n_chunks; ++c) {
+        if (warp == 0 && g.withhold != 1) issue_load(c);
+        if (g.withhold != 1) pend_load[c] = c;
+    }
+    for (int ch = 0; ch < n_chunks; ++ch) {
+        const int st = ch % stages;
+        const uint32_t parity = (uint32_t)((ch / stages) & 1);
+        if (!__syncthreads_and(mbar_wait(&bars[st], parity, limit))) {
             err = ERR_LOAD_TIMEOUT;
             break;
         }
-        loads_pending = false;
+        pend_load[st] = -1;
         tc_fence_after();
         if (tid == 0 && g.withhold != 2) {
-            const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+            const uint32_t a0 = smem_addr(stage_a(st)), b0 = a0 + (uint32_t)kTileM * (uint32_t)g.kchunk * 2u;
             for (int s = 0; s < g.kchunk / 16; ++s) {
                 const uint64_t ad = smem_desc(a0 + (uint32_t)s * 256u, 128u, rg_bytes);
                 const uint64_t bd = smem_desc(b0 + (uint32_t)s * 256u, 128u, rg_bytes);
                 mma_bf16(tmem_d, ad, bd, idesc, (ch > 0 || s > 0) ? 1u : 0u);
             }
-            mma_commit(&bars[1]);
+            mma_commit(&bars[2 + st]);   // arrives once every MMA issued so far has completed
         }
-        mma_pending = g.withhold != 2;
+        if (g.withhold != 2) pend_mma = ch;
         __syncwarp();
-        if (!__syncthreads_and(mbar_wait(&bars[1], parity, limit))) {
-            err = ERR_MMA_TIMEOUT;
-            break;
+        // stage st is reused by chunk ch + stages once these MMAs have read
+        // it; the last chunk's MMAs must be complete before the epilogue
+        if (ch + stages < n_chunks || ch == n_chunks - 1) {
+            if (!__syncthreads_and(mbar_wait(&bars[2 + st], parity, limit))) {
+                err = ERR_MMA_TIMEOUT;
+                break;
+            }
+            pend_mma = -1;   // commits are cumulative: every earlier MMA is done too
+            if (ch + stages < n_chunks) {
+                if (warp == 0 && g.withhold != 1) issue_load(ch + stages);
+                if (g.withhold != 1) pend_load[st] = ch + stages;
+            }
         }
-        mma_pending = false;
     }
     const bool ok = err == ERR_NONE;   // the same in every thread
     tc_fence_after();
@@ -268,8 +289,10 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ Ge
         if (tid == 0) atomicExch(g.error, err);
         // let our own copies and MMAs still in flight land (bounded) before the
         // CTA frees its tensor memory and leaves its shared memory
-        if (loads_pending) mbar_wait(&bars[0], (uint32_t)(ch & 1), kSpinLimit);
-        if (mma_pending) mbar_wait(&bars[1], (uint32_t)(ch & 1), kSpinLimit);
+        for (int st = 0; st < stages; ++st)
+            if (pend_load[st] >= 0) mbar_wait(&bars[st], (uint32_t)((pend_load[st] / stages) & 1), kSpinLimit);
+        if (pend_mma >= 0)
+            mbar_wait(&bars[2 + pend_mma % stages], (uint32_t)((pend_mma / stages) & 1), kSpinLimit);
     }
     tc_fence_before();
     __syncthreads();
@@ -319,7 +342,10 @@ cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s)
     const int ncols = a.ntile <= 32 ? 32 : (a.ntile <= 64 ? 64 : (a.ntile <= 128 ? 128 : 256));
     const size_t per_sm = 233472, reserve = 1024;
     const size_t cap_ctas = (size_t)(512 / ncols);
-    size_t smem = (size_t)(kTileM + a.ntile) * (size_t)g.kchunk * 2 + 128;
+    const size_t stage = (size_t)(kTileM + a.ntile) * (size_t)g.kchunk * 2;
+    const size_t max_dyn = 232448;   // 227 KB of dynamic shared memory per CTA
+    a.stages = (g.K / g.kchunk > 1 && 2 * stage + 128 <= max_dyn) ? 2 : 1;   // pipeline over several chunks
+    size_t smem = (size_t)a.stages * stage + 128;
     const size_t floor_bytes = per_sm / (cap_ctas + 1) + 1 - reserve;
     if (smem < floor_bytes) smem = floor_bytes;
     cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -13,7 +13,9 @@
 // epilogues and the pack kernels) write this layout directly, so each stage
 // of a GEMM is a few 1-D bulk copies (cp.async.bulk, the TMA's linear mode)
 // completing on an mbarrier; one elected thread then issues the MMAs and
-// commits them to a second mbarrier; four warps read the accumulator with
+// commits them to a second mbarrier (with two stages when the reduction spans
+// several chunks, so one chunk's copies land while the previous chunk's MMAs
+// run); four warps read the accumulator with
 // tcgen05.ld and run a fused epilogue.  Every wait is bounded: on timeout the
 // kernel records an error code, waits (bounded) for its own work in flight,
 // frees its tensor memory and returns.  Whether a wait ran out is decided for
@@ -60,6 +62,7 @@ struct GemmArgs {
     int *error;                // device error word (0 = ok)
     uint32_t spin_limit;       // polls per bounded wait (0: kSpinLimit)
     int withhold;              // failure-detection test: 1 no operand loads, 2 no MMAs (their waits run out)
+    int stages;                // shared-memory stages (1 or 2; set by launch_gemm)
 };
 
 // Failure-detection test setting applied by launch_gemm to every later GEMM

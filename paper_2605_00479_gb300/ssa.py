@@ -258,8 +258,8 @@ def tau_run(model, n_traj, x0, t_end, tau, sample_times, precision="fp64", round
     dev = torch.device("cuda", torch.cuda.current_device())
     K = st.size
     if out is None:
-        out = torch.empty((K, _stored(model, out_species), n_traj), dtype=torch.int16 if state_bytes == 2
-                          else torch.int32, device=dev)
+        out = torch.empty((K, model.N, n_traj), dtype=torch.int16 if state_bytes == 2 else torch.int32,
+                          device=dev)
     if status is None:
         status = torch.empty(n_traj, dtype=torch.int32, device=dev)
     if n_events is None:

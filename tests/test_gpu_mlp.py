@@ -18,11 +18,15 @@ def ssa():
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 16, 16), (300, 256, 256), (257, 128, 512), (1024, 256, 16), (64, 64, 32),
-                                   (384, 16, 768), (200, 192, 64), (130, 144, 48)])
+                                   (384, 16, 768), (200, 192, 64), (130, 144, 48), (256, 256, 2048),
+                                   (300, 240, 512), (129, 208, 768)])
 def test_gemm_matches_fp32_reference(ssa, M, N, K):
     """D = A B^T with bf16 operands and fp32 accumulation; the reference sums
     the same bf16 products in fp32 (differences come only from summation
-    order: |err| <= K * 2^-23 * sum|a||b|)."""
+    order: |err| <= K * 2^-23 * sum|a||b|).  K > 256 runs the two-stage
+    pipeline (copies of one chunk under the MMAs of the previous), except
+    where two stages of a wide column tile exceed shared memory (N = 240,
+    208: one stage)."""
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N * 3 + K)
     A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
     B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)

@@ -20,7 +20,7 @@ def test_surrogate_gain_over_ssa():
     from paper_2605_00479_gb300 import build
     build.build()
     from paper_2605_00479_gb300 import surrogate
-    r = surrogate.run(n_train=8192, traj_train=512, n_query=2048, steps=2000, batch_size=512, seed=11)
+    r = surrogate.run(n_train=8192, traj_train=512, n_query=4096, steps=2000, batch_size=512, seed=11)
     print(r)
     assert r["loss_last"] < r["loss_first"]
     # end to end, judge + network + re-simulation against the SSA alone

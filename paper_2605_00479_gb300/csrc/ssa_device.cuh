@@ -52,6 +52,16 @@ constexpr int kMaxK = 1024;
 #define SSA_MIN_BLOCKS 1
 #endif
 
+// Per kernel: the round-to-nearest kernels of the small compiled structures
+// (at most three species: birth-death, Schloegl, telegraph, dimer) in every
+// mode but fp64 fit 48 registers without spilling, so five 256-thread
+// blocks (40 warps) stay resident per SM instead of four (32 warps).  The
+// fp64, stochastic-rounding, repressilator and general kernels would spill.
+template <class Model, int PREC, int SR>
+struct KernelMinBlocks {
+    static constexpr int value = (SR == 0 && PREC != 0 && Model::N <= 3) ? 5 : SSA_MIN_BLOCKS;
+};
+
 enum Precision { FP64 = 0, FP32 = 1, MIXED_F16 = 2, MIXED_BF16 = 3, UNIFORM_F16 = 4, UNIFORM_BF16 = 5 };
 enum TrajStatus { ST_OVERFLOW = 1, ST_MAX_EVENTS = 2, ST_STATE_RANGE = 4, ST_NAN = 8 };
 
@@ -1126,7 +1136,7 @@ __device__ __forceinline__ void load_samples(const double *samples, int K, typen
 // ------------------------------------------------------------- the kernels
 // One model, one queue: arguments in parameter space.
 template <class Model, int PREC, int SR>
-__global__ void __launch_bounds__(256, SSA_MIN_BLOCKS) ssa_kernel(const __grid_constant__ RunArgs a)
+__global__ void __launch_bounds__(256, (KernelMinBlocks<Model, PREC, SR>::value)) ssa_kernel(const __grid_constant__ RunArgs a)
 {
     using P = typename ModeTraits<PREC>::P;
     __shared__ P smp[kMaxK];

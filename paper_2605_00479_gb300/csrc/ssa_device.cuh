@@ -52,14 +52,21 @@ constexpr int kMaxK = 1024;
 #define SSA_MIN_BLOCKS 1
 #endif
 
-// Per kernel: the round-to-nearest kernels of the small compiled structures
-// (at most three species: birth-death, Schloegl, telegraph, dimer) in every
-// mode but fp64 fit 48 registers without spilling, so five 256-thread
-// blocks (40 warps) stay resident per SM instead of four (32 warps).  The
-// fp64, stochastic-rounding, repressilator and general kernels would spill.
+// Per kernel: a register budget, as 256-thread blocks per SM, where it was
+// measured to pay (the A/B against uncapped builds, GB300).  The one-species
+// birth-death structure's round-to-nearest kernels (not fp64) fit 48
+// registers without spilling: five blocks (40 warps) instead of four, +16%.
+// For Schloegl, telegraph and dimer the same budget costs about 8% more
+// instructions and is slower; 64 registers for mixed stochastic rounding and
+// fp64 (-2%, -4%) and 80 for uniform stochastic rounding (0..+2%) did not pay
+// either.  Every other kernel keeps the compiler's choice.
+#ifndef SSA_KERNEL_BUDGETS
+#define SSA_KERNEL_BUDGETS 1   // 0: every kernel at SSA_MIN_BLOCKS (for comparisons)
+#endif
+
 template <class Model, int PREC, int SR>
 struct KernelMinBlocks {
-    static constexpr int value = (SR == 0 && PREC != 0 && Model::N <= 3) ? 5 : SSA_MIN_BLOCKS;
+    static constexpr int value = (SSA_KERNEL_BUDGETS && Model::N == 1 && SR == 0 && PREC != 0) ? 5 : SSA_MIN_BLOCKS;
 };
 
 enum Precision { FP64 = 0, FP32 = 1, MIXED_F16 = 2, MIXED_BF16 = 3, UNIFORM_F16 = 4, UNIFORM_BF16 = 5 };

@@ -107,21 +107,25 @@ def ops_per_event(prec, rnd):
 
 
 # ------------------------------------------------------------ ncu traffic
-# DRAM bytes (read + write) per trajectory of the headline kernel, from one
-# ncu count of a 3e5-trajectory launch scaled per trajectory (the traffic is
-# the snapshot stream, proportional to the trajectories).  Valid only for the kernel source it was measured on: the
-# key includes a hash of the device code, and a changed kernel reports null.
+# DRAM bytes (read + write) per trajectory of one headline ensemble call, from
+# one ncu count of a 4e5-trajectory call scaled per trajectory (the traffic is
+# the snapshot stream and the parked records, proportional to the
+# trajectories).  Valid only for the kernel source it was measured on: the key
+# includes a hash of the device code, and a changed kernel reports null.
 NCU_TRAFFIC_PER_TRAJ = {
-    # mixed_bf16 RN (the headline kernel), 3e5 trajectories, snapshots of X only,
-    # default launch shape: 39,469,056 B read + 49,828,864 B written
-    ("5ec6c4e2f23861d8", "mixed_bf16:rn"): (39469056 + 49828864) / 300000,
+    # mixed_bf16 RN (the headline kernel), 4e5 trajectories, snapshots of X only,
+    # default launch shape, longest-first split: launch 1 13,799,680 R +
+    # 13,164,288 W; ordering kernels 10,439,680 R; launch 2 86,931,968 R +
+    # 84,104,448 W
+    ("d5b5b68443360ab7", "mixed_bf16:rn"): (13799680 + 13164288 + 5218048 + 8448 + 5213184 + 86931968 + 84104448)
+    / 400000,
 }
 
 
 def device_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("ssa_device.cuh", "ssa_models.h", "ssa_launch.h"):
+    for f in ("ssa_device.cuh", "ssa_models.h", "ssa_launch.h", "ssa_order.cu"):
         with open(os.path.join(ROOT, "paper_2605_00479_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -392,9 +396,11 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     rec = {}
+    n0 = ssa.direct_kernel_launches()
     t0 = time.perf_counter()
     kernel_ms, step_ms = timed_steps(head, rec)
     wall = time.perf_counter() - t0
+    launches_main = ssa.direct_kernel_launches() - n0
     barrier(world)
     clocks.stop()
     local_time = sum(step_ms) / 1e3
@@ -407,7 +413,9 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     rec_all = {}
+    n0 = ssa.direct_kernel_launches()
     kernel_all, step_all = timed_steps(MODES16, rec_all)
+    launches_all = ssa.direct_kernel_launches() - n0
     barrier(world)
     clocks_all.stop()
     events_all = {k: float(sum(float(v[0]) for v in vals)) for k, vals in rec_all.items()}
@@ -480,8 +488,10 @@ def run_ours(args, world, rank, local):
 
     sms = torch.cuda.get_device_properties(local).multi_processor_count
 
-    def roofline(kms, evs, clk):
-        """ALU roofline of the step's dominant kernel (largest share)."""
+    def roofline(kms, evs, clk, launches):
+        """ALU roofline of the step's dominant kernel (largest share): its
+        operations over the whole call (with longest-first scheduling: both
+        launches of the kernel and the three ordering kernels between them)."""
         dom = max(kms, key=lambda k: sum(kms[k]))
         dom_ms = float(np.mean(kms[dom]))
         dom_events = evs[dom] / args.steps
@@ -490,9 +500,12 @@ def run_ours(args, world, rank, local):
         achieved = ops_per_event(*dom) * dom_events / (dom_ms / 1e3) / 1e9
         return {"bound": "alu", "kernel": f"ssa_kernel<schlogl,{dom[0]},{dom[1]}>",
                 "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-                "traffic": traffic_per_launch(f"{dom[0]}:{dom[1]}", N_TRAJ), "traffic_unit": "bytes per launch",
+                "traffic": traffic_per_launch(f"{dom[0]}:{dom[1]}", N_TRAJ),
+                "traffic_unit": "bytes per ensemble call (all its kernels)",
                 "source_hash": device_source_hash(),
                 "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock sampled in the run)",
+                "kernels_per_call": launches / (len(kms) * args.steps),
+                "timed": "CUDA events around each ensemble call on its stream (every kernel of the call)",
                 "snapshot_hbm_gbs": (K_SAMPLES * 1 * N_TRAJ * 4) / (dom_ms / 1e3) / 1e9}
 
     clk = clocks.summary()
@@ -508,22 +521,24 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": 1e3 * job_time / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": ",".join(sorted({p.split("_")[-1] for p, _ in head})),
         "data": "synthetic", "config": config_block(),
-        "gpu_launches": len(head) * args.steps,
-        "roofline": roofline(kernel_ms, events, clk),
+        "gpu_launches": launches_main,
+        "roofline": roofline(kernel_ms, events, clk, launches_main),
         "fp64_events_per_s": fp64_rate_job, "speedup_vs_fp64": value / fp64_rate_job,
         "ks_criterion": ks_block,
         "all_16bit_modes": {"value": all_events / all_time, "unit": "events/s",
                             "ms_per_step": 1e3 * all_time / args.steps, "steps": args.steps,
-                            "gpu_launches": len(MODES16) * args.steps,
+                            "gpu_launches": launches_all,
                             "speedup_vs_fp64": (all_events / all_time) / fp64_rate_job,
                             "modes": [f"{p}:{r}" for p, r in MODES16],
-                            "roofline": roofline(kernel_all, events_all, clocks_all.summary()),
+                            "roofline": roofline(kernel_all, events_all, clocks_all.summary(), launches_all),
                             "clocks": clocks_all.summary()},
         "modes": modes_out,
         "e2e": {"value": e2e_events / e2e_time, "unit": "events/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clk,
         "wall_s_timed": wall,
+        "scheduling": {"longest_first": args.longest_first,
+                       "kernels_per_call": launches_main / max(1, len(head) * args.steps)},
     }
     if world == 1 and not args.no_cpu_baseline:
         workers = os.cpu_count() or 1
@@ -998,9 +1013,11 @@ def run_models(args, world, rank, local, workload):
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
+    n_l0 = ssa.direct_kernel_launches()
     t0 = time.perf_counter()
     steps = [step(MODES16, SEED, n) for _ in range(args.steps)]
     wall = time.perf_counter() - t0
+    launches = ssa.direct_kernel_launches() - n_l0
     barrier(world)
     clocks.stop()
     local_time = sum(v[0] for st in steps for v in st.values()) / 1e3
@@ -1058,7 +1075,7 @@ def run_models(args, world, rank, local, workload):
         "metric": sp["metric"], "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * job_time / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16,bf16", "data": "synthetic", "config": sp["config"],
-        "gpu_launches": len(MODES16) * args.steps,
+        "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": f"ssa_kernel<{workload},{dom[0]},{dom[1]}>", "achieved": achieved,
                      "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
                      "traffic_unit": "bytes per launch", "source_hash": device_source_hash(),
@@ -1356,9 +1373,11 @@ def run_scale(args, world, rank, local):
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
+    n_l0 = ssa.direct_kernel_launches()
     t0 = time.perf_counter()
     steps = [{(prec, sb): launch(prec, sb, n) for prec, sb in SCALE_RUNS} for _ in range(args.steps)]
     wall = time.perf_counter() - t0
+    launches = ssa.direct_kernel_launches() - n_l0
     barrier(world)
     clocks.stop()
     local_time = sum(v[0] for stp in steps for v in stp.values()) / 1e3
@@ -1422,7 +1441,7 @@ def run_scale(args, world, rank, local):
                    "hbm_free_gb_before": free0 / 1e9,
                    "l2": f"each launch writes {SCALE_K * 6 * n * 2 / 1e9:.0f}-{SCALE_K * 6 * n * 4 / 1e9:.0f} GB of "
                          "snapshots (> 129 MB L2)"},
-        "gpu_launches": len(SCALE_RUNS) * args.steps,
+        "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": f"ssa_kernel<repressilator,{dom[0]},rn>", "achieved": achieved,
                      "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
                      "traffic_unit": "bytes per launch", "source_hash": device_source_hash(),
@@ -1456,7 +1475,13 @@ def main():
                     default="schlogl",
                     help="schlogl: the direct-method benchmark (default); tau: tau-leaping; rdme: spatial RDME; "
                          "birth_death / telegraph / dimer / repressilator: the other model types")
+    ap.add_argument("--longest-first", choices=["auto", "off", "on"], default="auto",
+                    help="scheduling of direct-method runs (ssa_set_longest_first): the library's automatic "
+                         "choice (default), never, or always")
     args = ap.parse_args()
+    if args.impl == "ours" and args.longest_first != "auto":
+        from paper_2605_00479_gb300 import ssa
+        ssa.set_longest_first(0 if args.longest_first == "off" else 2, 0)
     global N_TRAJ, MODES16
     if args.n_traj:
         N_TRAJ = args.n_traj

@@ -321,6 +321,41 @@ int ssa_set_tail_lock_limit(int spins);
 int ssa_tail_stats(int64_t *moved, int64_t *lock_timeouts, int64_t *resumed);
 
 /*
+ * ssa_set_longest_first -- scheduling of subsequent ssa_ensemble_run and
+ * ssa_ensemble_run_host calls.  A persistent launch ends when the trajectories
+ * that started last are done, and a long one among them keeps the GPU
+ * waiting on a few lanes.  Longest-first scheduling splits the run in two
+ * launches of the same kernel: the first runs every trajectory up to
+ * `park_events` events and parks those still unfinished (state, clock, next
+ * snapshot, and a predicted remaining work a0(x) * (t_end - t)); three small
+ * kernels sort the parked trajectories by that prediction; the second launch
+ * resumes them, largest first, so the launch ends on short ones.
+ *   mode         0 off; 1 automatic (the default: when a0(x0) * t_end >= 4096
+ *                events and there are at least 2 trajectories per resident
+ *                lane, 2 * SMs * 1024); 2 always
+ *   park_events  the parking point: 0 (the default) for a0(x0) * t_end / 5
+ *                (at least 256), else an even number >= 2; no split when it
+ *                is >= the run's max_events
+ * Random numbers are keyed by (trajectory id, event count) and a parked
+ * trajectory resumes whole, so results never depend on this; only speed
+ * does.  The split allocates its scratch (about 28 + 4 N bytes per
+ * trajectory) with stream-ordered allocation and runs one plain launch if
+ * that fails.  ssa_sweep_run_noalloc and batches never split.  Not
+ * synchronised with concurrent calls from other threads.  No paper
+ * counterpart.
+ * Errors: SSA_EINVAL (mode outside 0..2; park_events odd, or 1).
+ */
+int ssa_set_longest_first(int mode, int64_t park_events);
+
+/*
+ * ssa_direct_kernel_launches -- *count = kernels launched by
+ * ssa_ensemble_run and ssa_ensemble_run_host in this process so far (one per
+ * call, or five with longest-first scheduling: two direct-method launches and
+ * three ordering kernels).  Errors: SSA_EINVAL (count is NULL).
+ */
+int ssa_direct_kernel_launches(int64_t *count);
+
+/*
  * Batched heterogeneous runs: several groups, each a model with a sweep of
  * parameter sets, simulated by ONE persistent kernel with one device work
  * queue per group.  Lanes that finish a trajectory take the next one from

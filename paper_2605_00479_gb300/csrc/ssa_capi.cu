@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -67,6 +68,15 @@ bool g_cfg_set = false;
 ssa::LaunchConfig other_cfg() { return g_cfg_set ? g_cfg : kOtherDefault; }
 bool g_tail_compaction = true;
 int g_tail_lock_spins = 0;   // 0: the kernels' default bound
+
+// Longest-first scheduling of single-queue direct-method runs: 0 off,
+// 1 automatic (runs long and large enough for the launch tail to matter),
+// 2 always.  g_park_events: the parking point (0: a0(x0) t_end / 5).
+int g_longest_first = 1;
+int64_t g_park_events = 0;
+constexpr double kLongestFirstMinEvents = 4096.0;   // estimated events per trajectory
+constexpr int64_t kLongestFirstMinPerLane = 2;      // trajectories per resident lane
+std::atomic<long long> g_direct_launches{0};        // kernels launched by launch_run
 
 }  // namespace
 
@@ -259,10 +269,96 @@ void fill_structure(const ssa_model &m, int normalise, const int32_t *x0, ssa::R
     for (int i = 0; i < m.N; ++i) a.x0[i] = x0[i];
 }
 
-// One launch over trajectories traj_offset .. traj_offset + n_work - 1 whose
-// outputs sit in columns 0 .. n_work - 1 of arrays with `stride` columns
-// (out, status, n_events and t_final already point at the first column).
-// Arguments are validated by the caller.
+// Longest-first scheduling scratch: parked records, keys, the order and the
+// counters of the second launch, in one stream-ordered allocation.
+size_t longest_first_bytes(int64_t n, int N)
+{
+    const size_t n8 = (size_t)n * 8, n4 = (size_t)n * 4;
+    return 256 + 2 * n8 + (2 + (size_t)N) * n4 + (size_t)n + sizeof(unsigned) * ssa::kOrderBuckets +
+           sizeof(unsigned long long) * ssa::kOrderBuckets + 64;
+}
+
+ssa::LongestFirstScratch carve_longest_first(char *p, int64_t n, int N)
+{
+    ssa::LongestFirstScratch L;
+    L.head2 = reinterpret_cast<unsigned long long *>(p);
+    L.count = L.head2 + 1;
+    p += 256;
+    L.offs = reinterpret_cast<unsigned long long *>(p); p += sizeof(unsigned long long) * ssa::kOrderBuckets;
+    L.t = reinterpret_cast<double *>(p); p += (size_t)n * 8;
+    L.order = reinterpret_cast<int64_t *>(p); p += (size_t)n * 8;
+    L.hist = reinterpret_cast<unsigned *>(p); p += sizeof(unsigned) * ssa::kOrderBuckets;
+    L.k = reinterpret_cast<int32_t *>(p); p += (size_t)n * 4;
+    L.status = reinterpret_cast<uint32_t *>(p); p += (size_t)n * 4;
+    L.x = reinterpret_cast<int32_t *>(p); p += (size_t)n * 4 * (size_t)N;
+    L.parked = reinterpret_cast<uint8_t *>(p);
+    return L;
+}
+
+// The model as the ordering kernels see it: rate constants of the run (one
+// parameter set) in binary32, the structure, and the parked records.
+ssa::OrderModel order_model(const ssa::RunArgs &a, const ssa::LongestFirstScratch &L)
+{
+    ssa::OrderModel m;
+    std::memset(&m, 0, sizeof(m));
+    m.N = a.N;
+    m.M = a.M;
+    for (int j = 0; j < a.M; ++j) {
+        for (int i = 0; i < a.N; ++i) {
+            m.order[j][i] = a.order[j][i];
+            m.folded[j][i] = a.folded[j][i];
+        }
+        m.law[j] = a.law[j];
+        m.hill_h[j] = a.hill_h[j];
+        m.hill_reg[j] = a.hill_reg[j];
+        m.c[j] = (float)a.cprime[j];
+        m.h0[j] = (float)a.hill_a0[j];
+        m.h1[j] = (float)a.hill_a[j];
+    }
+    m.t_end = a.t_end;
+    m.x = L.x;
+    m.t = L.t;
+    m.parked = L.parked;
+    return m;
+}
+
+// Whether a single-queue run is split into park / order / resume, and with
+// which parking point; returns the scratch (null: one plain launch).  The
+// split pays when trajectories are long (the end of a persistent launch waits
+// for the trajectories that started last) and every lane runs several.  A
+// failed allocation falls back to the plain launch.
+char *plan_longest_first(const ssa_model &m, const int32_t *x0, int normalise, double t_end, int64_t n_work,
+                         int64_t max_events, cudaStream_t s, int64_t *park)
+{
+    if (g_longest_first == 0 || n_work < 1) return nullptr;
+    const double est = estimated_events(m, x0, normalise, t_end);
+    int64_t pe = g_park_events;
+    if (pe <= 0) {
+        const double p = est / 5.0;
+        pe = p < 256.0 ? 256 : (p > 1073741824.0 ? 1073741824 : (int64_t)p);
+    }
+    pe &= ~(int64_t)1;   // even: parked between step pairs
+    if (pe < 2 || pe >= max_events) return nullptr;
+    if (g_longest_first == 1) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return nullptr;
+        if (!(est >= kLongestFirstMinEvents) || n_work < kLongestFirstMinPerLane * (int64_t)sms * 1024) return nullptr;
+    }
+    char *p = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&p), longest_first_bytes(n_work, m.N), s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    *park = pe;
+    return p;
+}
+
+// Simulate trajectories traj_offset .. traj_offset + n_work - 1 whose outputs
+// sit in columns 0 .. n_work - 1 of arrays with `stride` columns (out,
+// status, n_events and t_final already point at the first column): one
+// persistent launch, or park / order / resume (longest-first scheduling,
+// above) with the same results.  Arguments are validated by the caller.
 int launch_run(const ssa_model *model, int64_t n_work, int64_t stride, uint64_t traj_offset, const int32_t *x0,
                double t_end, int n_samples, const double *sample_times, int precision, int rounding, int normalise,
                uint64_t seed, int64_t max_events, int state_bytes, uint32_t out_species, void *out,
@@ -309,7 +405,46 @@ int launch_run(const ssa_model *model, int64_t n_work, int64_t stride, uint64_t 
     a->tail_stats = tail_counters();
     a->lock_spins = g_tail_lock_spins;
     int grid = 0;
-    e = launcher_for(model->family)(*a, precision, rounding, normalise ? 1 : 0, g_cfg, s, &grid);
+    const int norm = normalise ? 1 : 0;
+    const ssa::Launcher launch = launcher_for(model->family);
+    int64_t park = 0;
+    char *scratch = plan_longest_first(*model, x0, normalise, t_end, n_work, max_events, s, &park);
+    if (scratch) {
+        // launch 1: every trajectory up to `park` events; the unfinished are parked
+        ssa::LongestFirstScratch L = carve_longest_first(scratch, n_work, model->N);
+        a->max_events = park;
+        a->cap_events = max_events;
+        a->park_t = L.t;
+        a->park_k = L.k;
+        a->park_status = L.status;
+        a->park_x = L.x;
+        a->parked = L.parked;
+        e = cudaMemsetAsync(L.parked, 0, (size_t)n_work, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.head2, 0, sizeof(unsigned long long), s);
+        if (e == cudaSuccess) e = launch(*a, precision, rounding, norm, g_cfg, s, &grid);
+        int launched = 1;
+        if (e == cudaSuccess) {
+            ssa::OrderModel om = order_model(*a, L);
+            e = ssa::launch_order(om, n_work, L.hist, L.offs, L.count, L.order, s, &launched);
+        }
+        if (e == cudaSuccess) {
+            // launch 2: the parked trajectories, largest predicted remaining work first
+            a->max_events = max_events;
+            a->cap_events = 0;
+            a->parked = nullptr;
+            a->resume_order = L.order;
+            a->resume_count = L.count;
+            a->resume_events = park;
+            a->queue_head = L.head2;
+            e = launch(*a, precision, rounding, norm, g_cfg, s, &grid);
+            launched += 1;
+        }
+        g_direct_launches += launched;
+        cudaFreeAsync(scratch, s);
+    } else {
+        e = launch(*a, precision, rounding, norm, g_cfg, s, &grid);
+        g_direct_launches += 1;
+    }
     cudaError_t e2 = cudaFreeAsync(head, s);
     delete a;
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -352,6 +487,23 @@ int ssa_set_tail_lock_limit(int spins)
 {
     if (spins < 0) return fail(SSA_EINVAL, "spins must be >= 0");
     g_tail_lock_spins = spins;
+    return SSA_OK;
+}
+
+int ssa_set_longest_first(int mode, int64_t park_events)
+{
+    if (mode < 0 || mode > 2) return fail(SSA_EINVAL, "mode must be 0 (off), 1 (automatic) or 2 (always)");
+    if (park_events < 0 || (park_events > 0 && (park_events < 2 || (park_events & 1))))
+        return fail(SSA_EINVAL, "park_events must be 0 (automatic) or an even number >= 2");
+    g_longest_first = mode;
+    g_park_events = park_events;
+    return SSA_OK;
+}
+
+int ssa_direct_kernel_launches(int64_t *count)
+{
+    if (!count) return fail(SSA_EINVAL, "count is NULL");
+    *count = (int64_t)g_direct_launches.load();
     return SSA_OK;
 }
 

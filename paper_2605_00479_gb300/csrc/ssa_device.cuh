@@ -117,6 +117,21 @@ struct RunArgs {
     unsigned long long *queue_head;    // zero before launch
     unsigned long long *tail_stats;    // [moved, lock waits given up, resumed at block end]; null: no tail compaction
     int lock_spins;                    // bound on one hand-off lock wait (0: kPoolLockSpins)
+    // Longest-first scheduling: two launches of the same kernel.  Launch 1
+    // (parked set) runs every trajectory up to max_events events, here the
+    // parking point, and parks those still unfinished there (state, clock,
+    // next snapshot); launch 2 (resume_order set) resumes the parked
+    // trajectories in the order the ordering kernels chose (largest
+    // predicted remaining work first).
+    int64_t cap_events;                // launch 1: the caller's event cap
+    double *park_t;                    // [n_work] clock at parking
+    int32_t *park_k;                   // [n_work] next snapshot
+    uint32_t *park_status;             // [n_work]
+    int32_t *park_x;                   // [N][n_work] state
+    uint8_t *parked;                   // [n_work] set to 1 when parked (zero before launch 1); null: no parking
+    const int64_t *resume_order;       // launch 2: items to resume, largest key first; null: items 0 .. n_work-1
+    const unsigned long long *resume_count;   // launch 2: entries of resume_order
+    int64_t resume_events;             // launch 2: events every parked trajectory has fired
 };
 
 // ------------------------------------------------------------------ Philox
@@ -556,6 +571,58 @@ __device__ void init_lane(const RunArgs &a, Lane<Model, PREC> &L, int64_t item, 
     L.active = true;
 }
 
+// Longest-first scheduling, launch 1: park an unfinished trajectory at the
+// parking point (between step pairs: L.n is even).  Its priority is computed
+// by the ordering kernels from the parked state.  The stores sit out of line,
+// with the state passed by value, so the step keeps its registers.
+static __device__ __noinline__ void park_store(const RunArgs &a, int64_t it, double t, int k, uint32_t status,
+                                               int x0, int x1, int x2, int x3, int x4, int x5, int x6, int x7)
+{
+    const int x[kMaxN] = {x0, x1, x2, x3, x4, x5, x6, x7};
+    a.parked[it] = 1u;
+    a.park_t[it] = t;
+    a.park_k[it] = k;
+    a.park_status[it] = status;
+#pragma unroll
+    for (int i = 0; i < kMaxN; ++i)
+        if (i < a.N) a.park_x[(int64_t)i * a.n_work + it] = x[i];
+}
+
+template <class Model, int PREC>
+__device__ __forceinline__ void park(const RunArgs &a, Lane<Model, PREC> &L)
+{
+    static_assert(kMaxN == 8, "park_store takes eight species");
+    int v[kMaxN];
+    unroll<kMaxN>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if constexpr (i < Model::N) v[i] = L.x[i];
+        else v[i] = 0;
+    });
+    park_store(a, L.item, (double)L.t, L.k, L.status, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]);
+    L.active = false;
+}
+
+// Longest-first scheduling, launch 2: continue a parked trajectory.  Every
+// quantity a lane holds besides (x, t, n, k, status) is a function of the
+// item, and random numbers are keyed by (trajectory id, n), so the resumed
+// trajectory is the same one an unparked run produces.
+template <class Model, int PREC>
+__device__ __forceinline__ void resume_lane(const RunArgs &a, Lane<Model, PREC> &L, int64_t item,
+                                            const typename ModeTraits<PREC>::P *smp)
+{
+    using P = typename ModeTraits<PREC>::P;
+    init_lane<Model, PREC>(a, L, item, smp);
+    L.n = a.resume_events;
+    L.t = (P)a.park_t[item];
+    L.k = a.park_k[item];
+    L.status = a.park_status[item];
+    unroll<Model::N>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (i < a.N) L.x[i] = a.park_x[(int64_t)i * a.n_work + item];
+    });
+    L.s_next = L.k < a.K ? smp[L.k] : P(__int_as_float(0x7F800000));
+}
+
 // ------------------------------------------------------------ one SSA step
 // Executes step n = L.n with uniform words (w0, w1).  Returns with L.active
 // cleared when the trajectory has finished (results written).
@@ -568,6 +635,10 @@ __device__ __forceinline__ void ssa_step(const RunArgs &a, Lane<Model, PREC> &L,
     constexpr int M = Model::M;
 
     if (L.n >= a.max_events) {
+        if (a.parked && L.n < a.cap_events) {
+            park<Model, PREC>(a, L);
+            return;
+        }
         L.status |= ST_MAX_EVENTS;
         finish<Model, PREC>(a, L);
         return;
@@ -803,6 +874,10 @@ __device__ __noinline__ void ssa_step_general(const RunArgs &a, Lane<GeneralMode
     const P kInf = P(__int_as_float(0x7F800000));
 
     if (L.n >= a.max_events) {
+        if (a.parked && L.n < a.cap_events) {
+            park<GeneralModel, PREC>(a, L);
+            return;
+        }
         L.status |= ST_MAX_EVENTS;
         finish<GeneralModel, PREC>(a, L);
         return;
@@ -1108,8 +1183,14 @@ __device__ __forceinline__ void run_queue(const RunArgs &a, const typename ModeT
             base = __shfl_sync(0xFFFFFFFFu, base, leader);
             if (!L.active && !drained) {
                 const unsigned long long item = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-                if (item < (unsigned long long)a.n_work) init_lane<Model, PREC>(a, L, (int64_t)item, smp);
-                else drained = true;
+                if (a.resume_order) {
+                    if (item < *a.resume_count) resume_lane<Model, PREC>(a, L, a.resume_order[item], smp);
+                    else drained = true;
+                } else if (item < (unsigned long long)a.n_work) {
+                    init_lane<Model, PREC>(a, L, (int64_t)item, smp);
+                } else {
+                    drained = true;
+                }
             }
         }
         // the pool's count may change between lanes' reads: decide by ballot, warp-uniformly

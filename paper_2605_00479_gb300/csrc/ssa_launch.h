@@ -27,6 +27,40 @@ cudaError_t launch_telegraph(const RunArgs &, int, int, int, LaunchConfig, cudaS
 cudaError_t launch_dimer(const RunArgs &, int, int, int, LaunchConfig, cudaStream_t, int *);
 cudaError_t launch_repressilator(const RunArgs &, int, int, int, LaunchConfig, cudaStream_t, int *);
 
+// Longest-first scheduling (ssa_order.cu): order the parked items by
+// descending predicted remaining work into order[0 .. *count-1].  hist
+// [kOrderBuckets] and offs [kOrderBuckets] are scratch.  Adds the kernels it
+// launched to *launches.
+constexpr int kOrderBuckets = 1024;
+struct OrderModel {
+    int N, M;
+    int8_t order[kMaxM][kMaxN];
+    int8_t folded[kMaxM][kMaxN];
+    int8_t law[kMaxM];
+    int8_t hill_h[kMaxM];
+    int8_t hill_reg[kMaxM];
+    float c[kMaxM];              // c'_j (mass action), binary32
+    float h0[kMaxM], h1[kMaxM];  // Hill alpha0, alpha
+    double t_end;
+    const int32_t *x;            // parked state [N][n]
+    const double *t;             // parked clock [n]
+    const uint8_t *parked;       // [n] nonzero: parked
+};
+struct LongestFirstScratch {
+    unsigned long long *head2;   // work-queue counter of launch 2
+    unsigned long long *count;   // parked trajectories
+    unsigned long long *offs;    // [kOrderBuckets]
+    unsigned *hist;              // [kOrderBuckets]
+    double *t;                   // [n] parked records (RunArgs::park_*)
+    int32_t *k;
+    uint32_t *status;
+    int32_t *x;                  // [N][n]
+    uint8_t *parked;             // [n]
+    int64_t *order;              // [n]
+};
+cudaError_t launch_order(const OrderModel &m, int64_t n, unsigned *hist, unsigned long long *offs,
+                         unsigned long long *count, int64_t *order, cudaStream_t stream, int *launches);
+
 // Tau-leaping kernel (ssa_k_tau.cu): precision `prec`, rounding `sr` (0 RN,
 // 1 SR), leap a.tau, a.n_leaps leaps.
 cudaError_t launch_tau(const RunArgs &a, int prec, int sr, LaunchConfig cfg, cudaStream_t stream, int *grid_out);

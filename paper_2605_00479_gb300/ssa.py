@@ -38,6 +38,8 @@ SIGNATURES = {
     "ssa_set_tail_compaction": (_I, [_I]),
     "ssa_set_tail_lock_limit": (_I, [_I]),
     "ssa_tail_stats": (_I, [ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "ssa_set_longest_first": (_I, [_I, _I64]),
+    "ssa_direct_kernel_launches": (_I, [ctypes.POINTER(_I64)]),
     "ssa_batch_create": (_I, [_I, _P, _D, _I, _P, _I, _I, _I, _U64, _I64, _I, ctypes.POINTER(_P)]),
     "ssa_batch_launch": (_I, [_P, _P]),
     "ssa_batch_autotune": (_I, [_P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -173,6 +175,19 @@ def tail_stats():
     moved, timeouts, resumed = _I64(0), _I64(0), _I64(0)
     _check(lib().ssa_tail_stats(ctypes.byref(moved), ctypes.byref(timeouts), ctypes.byref(resumed)))
     return int(moved.value), int(timeouts.value), int(resumed.value)
+
+
+def set_longest_first(mode=1, park_events=0):
+    """Scheduling of direct-method ensemble runs: 0 off, 1 automatic (the
+    default), 2 always; park_events 0 for the automatic parking point."""
+    _check(lib().ssa_set_longest_first(int(mode), int(park_events)))
+
+
+def direct_kernel_launches():
+    """Kernels launched by the direct-method ensemble entry points so far."""
+    n = _I64(0)
+    _check(lib().ssa_direct_kernel_launches(ctypes.byref(n)))
+    return int(n.value)
 
 
 def _run_scalars(model, n_traj, traj_offset, x0, t_end, sample_times, precision, rounding, normalise, seed,

@@ -123,6 +123,20 @@ def test_tail_compaction_switch_validation(ssa):
     ssa.set_tail_compaction(True)
 
 
+def test_longest_first_switch_validation(ssa):
+    L = ssa.lib()
+    assert L.ssa_set_longest_first(3, 0) == ssa.SSA_EINVAL
+    assert L.ssa_set_longest_first(-1, 0) == ssa.SSA_EINVAL
+    assert L.ssa_set_longest_first(2, 1) == ssa.SSA_EINVAL      # odd: would park inside a step pair
+    assert L.ssa_set_longest_first(2, 4097) == ssa.SSA_EINVAL
+    assert L.ssa_set_longest_first(2, -2) == ssa.SSA_EINVAL
+    ssa.set_longest_first(2, 2)
+    ssa.set_longest_first(0, 0)
+    ssa.set_longest_first()
+    assert L.ssa_direct_kernel_launches(None) == ssa.SSA_EINVAL
+    assert ssa.direct_kernel_launches() >= 0
+
+
 def test_batch_create_rejects_before_allocating(ssa):
     """Group validation happens on the host before any device allocation."""
     m = ssa.Model.from_dict(P.telegraph())

@@ -583,16 +583,16 @@ RDME_CAP = 4_000_000
 # hash, workload, mode); a changed kernel reports null until re-counted.
 NCU_PER_UNIT = {
     # tau, 2e5 trajectories, one launch per mode (compiled Schloegl structure)
-    ("1dfdc0e0bd74bdda", "tau", "fp32:rn"): {"warp_inst": 6.2743, "dram_bytes": 0.01301},
-    ("1dfdc0e0bd74bdda", "tau", "mixed_f16:rn"): {"warp_inst": 6.3621, "dram_bytes": 0.01427},
-    ("1dfdc0e0bd74bdda", "tau", "mixed_bf16:rn"): {"warp_inst": 6.2441, "dram_bytes": 0.01374},
-    ("1dfdc0e0bd74bdda", "tau", "uniform_f16:sr"): {"warp_inst": 6.5411, "dram_bytes": 0.01405},
-    ("1dfdc0e0bd74bdda", "tau", "uniform_bf16:sr"): {"warp_inst": 6.4396, "dram_bytes": 0.01375},
+    ("e5551c9acd37523b", "tau", "fp32:rn"): {"warp_inst": 6.2743, "dram_bytes": 0.01315},
+    ("e5551c9acd37523b", "tau", "mixed_f16:rn"): {"warp_inst": 6.3621, "dram_bytes": 0.01422},
+    ("e5551c9acd37523b", "tau", "mixed_bf16:rn"): {"warp_inst": 6.2441, "dram_bytes": 0.01362},
+    ("e5551c9acd37523b", "tau", "uniform_f16:sr"): {"warp_inst": 6.5411, "dram_bytes": 0.01386},
+    ("e5551c9acd37523b", "tau", "uniform_bf16:sr"): {"warp_inst": 6.4396, "dram_bytes": 0.01355},
     # rdme, 32768 lattices, one launch per mode
-    ("3677482804b65c5a", "rdme", "fp32:rn"): {"warp_inst": 30.1687, "dram_bytes": 0.00010},
-    ("3677482804b65c5a", "rdme", "mixed_f16:rn"): {"warp_inst": 32.4930, "dram_bytes": 0.00016},
-    ("3677482804b65c5a", "rdme", "mixed_bf16:rn"): {"warp_inst": 32.5187, "dram_bytes": 0.00063},
-    ("3677482804b65c5a", "rdme", "mixed_f16:sr"): {"warp_inst": 43.9234, "dram_bytes": 0.00111},
+    ("0e6116215f156622", "rdme", "fp32:rn"): {"warp_inst": 30.1687, "dram_bytes": 0.00003},
+    ("0e6116215f156622", "rdme", "mixed_f16:rn"): {"warp_inst": 32.4930, "dram_bytes": 0.00016},
+    ("0e6116215f156622", "rdme", "mixed_bf16:rn"): {"warp_inst": 32.5187, "dram_bytes": 0.00061},
+    ("0e6116215f156622", "rdme", "mixed_f16:sr"): {"warp_inst": 43.9234, "dram_bytes": 0.00103},
 }
 
 
@@ -1029,8 +1029,13 @@ def run_models(args, world, rank, local, workload):
     r64 = step([("fp64", "rn")], SEED + 1, n64)[("fp64", "rn")]
     fp64_rate = r64[1] / (r64[0] / 1e3)
 
-    # end to end through the host-buffer entry point (pinned host memory)
+    # end to end through the host-buffer entry point (pinned host memory); one
+    # untimed call first (the entry point's staging memory pool grows once per
+    # process)
     h = [torch.empty(v.shape, dtype=v.dtype).pin_memory() for v in bufs[MODES16[0]]]
+    ssa.ensemble_run_host(model, n, x0, sp["t_end"], sp["samples"], MODES16[0][0], MODES16[0][1], False, SEED,
+                          sp["cap"], 4, out=h[0].numpy(), status=h[1].numpy().view(np.uint32), n_events=h[2].numpy(),
+                          t_final=h[3].numpy(), traj_offset=offset)
     e2e_events, e2e_time, h2d, d2h = 0.0, 0.0, 0, 0
     for prec, rnd in MODES16:
         t1 = time.perf_counter()

@@ -1037,12 +1037,15 @@ def run_models(args, world, rank, local, workload):
                           sp["cap"], 4, out=h[0].numpy(), status=h[1].numpy().view(np.uint32), n_events=h[2].numpy(),
                           t_final=h[3].numpy(), traj_offset=offset)
     e2e_events, e2e_time, h2d, d2h = 0.0, 0.0, 0, 0
+    e2e_ms = {}
     for prec, rnd in MODES16:
         t1 = time.perf_counter()
         ssa.ensemble_run_host(model, n, x0, sp["t_end"], sp["samples"], prec, rnd, False, SEED, sp["cap"], 4,
                               out=h[0].numpy(), status=h[1].numpy().view(np.uint32), n_events=h[2].numpy(),
                               t_final=h[3].numpy(), traj_offset=offset)
-        e2e_time += time.perf_counter() - t1
+        dt = time.perf_counter() - t1
+        e2e_time += dt
+        e2e_ms[f"{prec}:{rnd}"] = 1e3 * dt
         e2e_events += float(h[2].numpy().sum())
         h2d += x0.nbytes + np.asarray(sp["samples"]).nbytes
         d2h += sum(v.numel() * v.element_size() for v in h)
@@ -1094,7 +1097,7 @@ def run_models(args, world, rank, local, workload):
                                            if modes_out[f"{p}:{r}"]["ks_p_vs_fp64_n1e4"] > 0.05]},
         "modes": modes_out,
         "e2e": {"value": e2e_events / e2e_time, "unit": "events/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h), "ms_per_call": e2e_ms},
         "clocks": clk, "wall_s_timed": wall,
     }
     if world == 1 and not args.no_cpu_baseline:

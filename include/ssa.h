@@ -338,9 +338,15 @@ int ssa_tail_stats(int64_t *moved, int64_t *lock_timeouts, int64_t *resumed);
  *                is >= the run's max_events
  * Random numbers are keyed by (trajectory id, event count) and a parked
  * trajectory resumes whole, so results never depend on this; only speed
- * does.  The split allocates its scratch (about 28 + 4 N bytes per
+ * does.  The split allocates its scratch (about 29 + 4 N bytes per
  * trajectory) with stream-ordered allocation and runs one plain launch if
- * that fails.  ssa_sweep_run_noalloc and batches never split.  Not
+ * that fails.  ssa_batch_create applies the setting in force when it is
+ * called, per group, to that batch's launches: a group parks by the same
+ * rule with its mean a0(x0) * t_end over its sets (the ordering uses each
+ * set's own rate constants), the batch's scratch is part of its device
+ * tables, and ssa_batch_launch then runs launch 1, the ordering kernels of
+ * every parking group and launch 2 (all captured in its graph); the
+ * autotuner times plain launches.  ssa_sweep_run_noalloc never splits.  Not
  * synchronised with concurrent calls from other threads.  No paper
  * counterpart.
  * Errors: SSA_EINVAL (mode outside 0..2; park_events odd, or 1).
@@ -349,9 +355,10 @@ int ssa_set_longest_first(int mode, int64_t park_events);
 
 /*
  * ssa_direct_kernel_launches -- *count = kernels launched by
- * ssa_ensemble_run and ssa_ensemble_run_host in this process so far (one per
- * call, or five with longest-first scheduling: two direct-method launches and
- * three ordering kernels).  Errors: SSA_EINVAL (count is NULL).
+ * ssa_ensemble_run, ssa_ensemble_run_host and ssa_batch_launch in this
+ * process so far: one per call, or with longest-first scheduling two
+ * direct-method launches plus three ordering kernels (per parking group for
+ * a batch).  Errors: SSA_EINVAL (count is NULL).
  */
 int ssa_direct_kernel_launches(int64_t *count);
 
@@ -396,15 +403,19 @@ typedef struct {
 typedef struct ssa_batch ssa_batch;   /* opaque, owned by the library */
 
 /* Validate the groups, compute every set's c' in binary64, upload the
- * per-set tables to device memory owned by the batch (synchronous).
+ * per-set tables to device memory owned by the batch (synchronous), and
+ * decide per group whether its launches park and resume longest-first
+ * (ssa_set_longest_first; the scratch, about 29 + 4 N bytes per trajectory
+ * of a parking group, is part of the batch's device memory).
  * n_groups in 1..16.  Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA. */
 int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, int n_samples,
                      const double *sample_times, int precision, int rounding, int normalise,
                      uint64_t seed, int64_t max_events, int state_bytes, ssa_batch **out);
 
 /* Run the whole batch on `stream`.  On a non-NULL stream the queue reset and
- * the kernel are captured once into a CUDA graph and replayed on later calls;
- * on the NULL stream they are launched directly.  Asynchronous. */
+ * the kernels (one launch, or launch 1, the ordering kernels and launch 2
+ * when groups park) are captured once into a CUDA graph and replayed on
+ * later calls; on the NULL stream they are launched directly.  Asynchronous. */
 int ssa_batch_launch(ssa_batch *batch, void *stream);
 
 /* Pick threads per block, resident blocks per SM and step pairs per refill

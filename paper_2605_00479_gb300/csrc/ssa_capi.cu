@@ -315,6 +315,10 @@ ssa::OrderModel order_model(const ssa::RunArgs &a, const ssa::LongestFirstScratc
         m.h0[j] = (float)a.hill_a0[j];
         m.h1[j] = (float)a.hill_a[j];
     }
+    m.n_sets = a.n_sets;
+    m.traj_per_set = a.traj_per_set;
+    m.cprime_tab = a.cprime_tab;
+    m.hill_tab = a.hill_tab;
     m.t_end = a.t_end;
     m.x = L.x;
     m.t = L.t;
@@ -902,10 +906,20 @@ struct ssa_batch {
     ssa::RunArgs *d_groups;
     ssa::RunArgs *d_tune_groups;
     unsigned long long *d_heads;
-    ssa::RunArgs *h_groups;   // host copies [n_groups]
+    ssa::RunArgs *h_groups;   // host copies [n_groups] (one launch, no parking)
     ssa::BatchArgs *args;
     cudaGraphExec_t exec;
     bool graph_valid;
+    int graph_kernels;                    // kernels in the captured graph
+    // longest-first scheduling: launch 1 from d_groups (parking groups get
+    // their parking point as the cap), ordering kernels per parking group,
+    // launch 2 from d_groups2
+    bool split;
+    ssa::RunArgs *d_groups2;
+    unsigned long long *d_zero;           // resume count of the groups that do not park
+    int64_t *park;                        // host [n_groups]: parking point, 0 = not parked
+    ssa::LongestFirstScratch *lf;         // host [n_groups]
+    ssa::OrderModel *om;                  // host [n_groups]
 };
 
 namespace {
@@ -935,16 +949,80 @@ void batch_free(ssa_batch *b)
     if (b->graph_valid) cudaGraphExecDestroy(b->exec);
     if (b->dmem) cudaFree(b->dmem);
     delete[] b->h_groups;
+    delete[] b->park;
+    delete[] b->lf;
+    delete[] b->om;
     delete b->args;
     delete b;
 }
 
-cudaError_t batch_enqueue(ssa_batch *b, const ssa::BatchArgs &args, ssa::LaunchConfig cfg, cudaStream_t s)
+// Launch-1 and launch-2 arguments from the plain ones (h_groups), uploaded to
+// d_groups and d_groups2; without the split, d_groups gets the plain ones.
+cudaError_t batch_upload(ssa_batch *b)
+{
+    const size_t bytes = sizeof(ssa::RunArgs) * (size_t)b->n_groups;
+    if (!b->split) return cudaMemcpy(b->d_groups, b->h_groups, bytes, cudaMemcpyHostToDevice);
+    std::vector<ssa::RunArgs> p1(b->h_groups, b->h_groups + b->n_groups), p2 = p1;
+    for (int g = 0; g < b->n_groups; ++g) {
+        const ssa::LongestFirstScratch &L = b->lf[g];
+        if (b->park[g] > 0) {
+            p1[g].max_events = b->park[g];
+            p1[g].cap_events = b->h_groups[g].max_events;
+            p1[g].park_t = L.t;
+            p1[g].park_k = L.k;
+            p1[g].park_status = L.status;
+            p1[g].park_x = L.x;
+            p1[g].parked = L.parked;
+            p2[g].park_t = L.t;   // launch 2 reads the parked records
+            p2[g].park_k = L.k;
+            p2[g].park_status = L.status;
+            p2[g].park_x = L.x;
+            p2[g].resume_order = L.order;
+            p2[g].resume_count = L.count;
+            p2[g].resume_events = b->park[g];
+            p2[g].queue_head = L.head2;
+        } else {   // finished in launch 1: nothing to resume
+            p2[g].resume_order = reinterpret_cast<const int64_t *>(b->d_zero);
+            p2[g].resume_count = b->d_zero;
+        }
+    }
+    cudaError_t e = cudaMemcpy(b->d_groups, p1.data(), bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_groups2, p2.data(), bytes, cudaMemcpyHostToDevice);
+    return e;
+}
+
+// One batched run on stream s: one launch, or (split) launch 1, the ordering
+// kernels of every parking group and launch 2.  Stream-ordered throughout,
+// so it can be captured in a graph.  Adds the kernels it launched to
+// *launches.
+cudaError_t batch_enqueue(ssa_batch *b, const ssa::BatchArgs &args, ssa::LaunchConfig cfg, cudaStream_t s,
+                          bool split, int *launches)
 {
     cudaError_t e = cudaMemsetAsync(b->d_heads, 0, sizeof(unsigned long long) * (size_t)b->n_groups, s);
     if (e != cudaSuccess) return e;
     int grid = 0;
-    return ssa::launch_batch(args, b->work, b->precision, b->rounding, b->compact, cfg, s, &grid);
+    if (!split) {
+        if (launches) *launches += 1;
+        return ssa::launch_batch(args, b->work, b->precision, b->rounding, b->compact, cfg, s, &grid);
+    }
+    for (int g = 0; g < b->n_groups && e == cudaSuccess; ++g) {
+        if (b->park[g] <= 0) continue;
+        e = cudaMemsetAsync(b->lf[g].parked, 0, (size_t)b->h_groups[g].n_work, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->lf[g].head2, 0, sizeof(unsigned long long), s);
+    }
+    if (e == cudaSuccess) e = ssa::launch_batch(args, b->work, b->precision, b->rounding, b->compact, cfg, s, &grid);
+    int n = 1;
+    for (int g = 0; g < b->n_groups && e == cudaSuccess; ++g)
+        if (b->park[g] > 0) e = ssa::launch_order(b->om[g], b->h_groups[g].n_work, b->lf[g].hist, b->lf[g].offs,
+                                                  b->lf[g].count, b->lf[g].order, s, &n);
+    if (e == cudaSuccess) {
+        ssa::BatchArgs a2 = args;
+        a2.groups = b->d_groups2;
+        e = ssa::launch_batch(a2, b->work, b->precision, b->rounding, b->compact, cfg, s, &grid);
+        n += 1;
+    }
+    if (launches) *launches += n;
+    return e;
 }
 
 }  // namespace
@@ -963,6 +1041,7 @@ int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, 
     size_t bytes = align_up(sizeof(ssa::RunArgs) * (size_t)n_groups, 256) * 2 + 256;
     int64_t work = 0;
     bool compact = true;
+    double est_events[ssa::kMaxGroups] = {0.0};
     for (int g = 0; g < n_groups; ++g) {
         const ssa_batch_group &G = groups[g];
         if (!G.model) return fail(SSA_EINVAL, "group %d: model is NULL", g);
@@ -992,7 +1071,44 @@ int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, 
         if (fam < 3) compact = false;
         work += items;
         bytes += group_tables(G.n_sets, G.model->M, G.model->N).total();
+        // mean estimated events per trajectory over the group's sets
+        double est = 0.0;
+        for (int64_t q = 0; q < G.n_sets; ++q) {
+            ssa_model mq = *G.model;
+            for (int j = 0; j < mq.M; ++j) {
+                if (G.rates) mq.rate[j] = G.rates[q * mq.M + j];
+                if (G.hill && mq.law[j] == SSA_LAW_HILL_REPRESSION)
+                    for (int c = 0; c < 2; ++c) mq.hill[j][c] = G.hill[(q * mq.M + j) * 2 + c];
+            }
+            est += estimated_events(mq, G.x0 + q * mq.N, normalise, t_end);
+        }
+        est_events[g] = est / (double)G.n_sets;
     }
+    // longest-first scheduling per group (as for single runs)
+    int64_t park[ssa::kMaxGroups] = {0};
+    bool split = false;
+    if (g_longest_first != 0 && work > 0) {
+        int dev = 0, sms = 0;
+        const bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+                        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+        const bool enough = g_longest_first == 2 || (ok && work >= kLongestFirstMinPerLane * (int64_t)sms * 1024);
+        for (int g = 0; g < n_groups && enough; ++g) {
+            const int64_t items = groups[g].n_sets * groups[g].traj_per_set;
+            if (items < 1) continue;
+            if (g_longest_first == 1 && !(est_events[g] >= kLongestFirstMinEvents)) continue;
+            int64_t pe = g_park_events;
+            if (pe <= 0) {
+                const double p = est_events[g] / 5.0;
+                pe = p < 256.0 ? 256 : (p > 1073741824.0 ? 1073741824 : (int64_t)p);
+            }
+            pe &= ~(int64_t)1;
+            if (pe < 2 || pe >= max_events) continue;
+            park[g] = pe;
+            split = true;
+            bytes += align_up(longest_first_bytes(items, groups[g].model->N), 256);
+        }
+    }
+    if (split) bytes += align_up(sizeof(ssa::RunArgs) * (size_t)n_groups, 256) + 256;
     ssa_batch *b = new (std::nothrow) ssa_batch;
     if (!b) return fail(SSA_ENOMEM, "out of host memory");
     std::memset(b, 0, sizeof(*b));
@@ -1005,7 +1121,11 @@ int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, 
     b->cfg = other_cfg();
     b->h_groups = new (std::nothrow) ssa::RunArgs[n_groups];
     b->args = new (std::nothrow) ssa::BatchArgs;
-    if (!b->h_groups || !b->args) {
+    b->split = split;
+    b->park = new (std::nothrow) int64_t[n_groups];
+    b->lf = new (std::nothrow) ssa::LongestFirstScratch[n_groups];
+    b->om = new (std::nothrow) ssa::OrderModel[n_groups];
+    if (!b->h_groups || !b->args || !b->park || !b->lf || !b->om) {
         batch_free(b);
         return fail(SSA_ENOMEM, "out of host memory");
     }
@@ -1023,6 +1143,18 @@ int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, 
     p += align_up(sizeof(ssa::RunArgs) * (size_t)n_groups, 256);
     b->d_heads = reinterpret_cast<unsigned long long *>(p);
     p += 256;
+    if (split) {
+        b->d_groups2 = reinterpret_cast<ssa::RunArgs *>(p);
+        p += align_up(sizeof(ssa::RunArgs) * (size_t)n_groups, 256);
+        b->d_zero = reinterpret_cast<unsigned long long *>(p);
+        p += 256;
+        e = cudaMemset(b->d_zero, 0, sizeof(unsigned long long));
+    }
+    for (int g = 0; g < n_groups; ++g) {
+        b->park[g] = park[g];
+        std::memset(&b->lf[g], 0, sizeof(b->lf[g]));
+        std::memset(&b->om[g], 0, sizeof(b->om[g]));
+    }
 
     std::memset(b->args, 0, sizeof(*b->args));
     b->args->n_groups = n_groups;
@@ -1088,9 +1220,18 @@ int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, 
         a.t_final = G.t_final;
         a.queue_head = b->d_heads + g;
         b->args->family[g] = (int8_t)m.family;
+        if (park[g] > 0) {
+            const size_t lb = align_up(longest_first_bytes(a.n_work, m.N), 256);
+            if ((size_t)(p - b->dmem) + lb > b->dmem_bytes) {
+                batch_free(b);
+                return fail(SSA_EINVAL, "internal: batch scratch layout exceeds its arena");
+            }
+            b->lf[g] = carve_longest_first(p, a.n_work, m.N);
+            b->om[g] = order_model(a, b->lf[g]);
+            p += lb;
+        }
     }
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_groups, b->h_groups, sizeof(ssa::RunArgs) * (size_t)n_groups, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = batch_upload(b);
     if (e != cudaSuccess) {
         batch_free(b);
         return cuda_fail(e, "batch upload");
@@ -1106,14 +1247,17 @@ int ssa_batch_launch(ssa_batch *b, void *stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (s == nullptr) {
-        e = batch_enqueue(b, *b->args, b->cfg, s);
+        int n = 0;
+        e = batch_enqueue(b, *b->args, b->cfg, s, b->split, &n);
+        g_direct_launches += n;
         return e == cudaSuccess ? SSA_OK : cuda_fail(e, "batch launch");
     }
     if (!b->graph_valid) {
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        const cudaError_t e1 = batch_enqueue(b, *b->args, b->cfg, s);
+        b->graph_kernels = 0;
+        const cudaError_t e1 = batch_enqueue(b, *b->args, b->cfg, s, b->split, &b->graph_kernels);
         e = cudaStreamEndCapture(s, &graph);
         if (e1 != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -1126,6 +1270,7 @@ int ssa_batch_launch(ssa_batch *b, void *stream)
         b->graph_valid = true;
     }
     e = cudaGraphLaunch(b->exec, s);
+    if (e == cudaSuccess) g_direct_launches += b->graph_kernels;
     return e == cudaSuccess ? SSA_OK : cuda_fail(e, "cudaGraphLaunch");
 }
 
@@ -1166,9 +1311,9 @@ int ssa_batch_autotune(ssa_batch *b, void *stream, int *threads_per_block, int *
                                     cudaMemcpyHostToDevice, s);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);
                 ssa::LaunchConfig cfg = {blk, ps, sl};
-                if (e == cudaSuccess) e = batch_enqueue(b, targs, cfg, s);   // warm
+                if (e == cudaSuccess) e = batch_enqueue(b, targs, cfg, s, false, nullptr);   // warm
                 if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-                if (e == cudaSuccess) e = batch_enqueue(b, targs, cfg, s);
+                if (e == cudaSuccess) e = batch_enqueue(b, targs, cfg, s, false, nullptr);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 if (e != cudaSuccess) {
@@ -1187,7 +1332,7 @@ int ssa_batch_autotune(ssa_batch *b, void *stream, int *threads_per_block, int *
     cudaEventDestroy(e1);
     b->cfg = best_cfg;
     for (int g = 0; g < b->n_groups; ++g) b->h_groups[g].slice_pairs = best_cfg.slice_pairs;
-    e = cudaMemcpy(b->d_groups, b->h_groups, sizeof(ssa::RunArgs) * (size_t)b->n_groups, cudaMemcpyHostToDevice);
+    e = batch_upload(b);
     if (e != cudaSuccess) return cuda_fail(e, "autotune upload");
     if (b->graph_valid) {
         cudaGraphExecDestroy(b->exec);

@@ -39,8 +39,12 @@ struct OrderModel {
     int8_t law[kMaxM];
     int8_t hill_h[kMaxM];
     int8_t hill_reg[kMaxM];
-    float c[kMaxM];              // c'_j (mass action), binary32
-    float h0[kMaxM], h1[kMaxM];  // Hill alpha0, alpha
+    float c[kMaxM];              // c'_j (mass action), binary32 (one parameter set)
+    float h0[kMaxM], h1[kMaxM];  // Hill alpha0, alpha (one parameter set)
+    int n_sets;                  // > 1: item i uses set i / traj_per_set from the tables below
+    int64_t traj_per_set;
+    const double *cprime_tab;    // [n_sets][M]
+    const double *hill_tab;      // [n_sets][M][2] or null
     double t_end;
     const int32_t *x;            // parked state [N][n]
     const double *t;             // parked clock [n]

@@ -33,6 +33,7 @@ __device__ __forceinline__ int key_bucket(float key)
 __device__ __forceinline__ int item_bucket(const OrderModel &m, int64_t i, int64_t n)
 {
     if (!m.parked[i]) return -1;
+    const int64_t set = m.n_sets > 1 ? i / m.traj_per_set : 0;
     float a0 = 0.0f;
 #pragma unroll 1
     for (int j = 0; j < m.M; ++j) {
@@ -41,9 +42,12 @@ __device__ __forceinline__ int item_bucket(const OrderModel &m, int64_t i, int64
             const float xr = (float)m.x[(int64_t)m.hill_reg[j] * n + i];
             float q = 1.0f;
             for (int r = 0; r < m.hill_h[j]; ++r) q *= xr;
-            v = m.h0[j] + m.h1[j] / (1.0f + q);
+            const bool tab = m.n_sets > 1 && m.hill_tab;
+            const float h0 = tab ? (float)m.hill_tab[(set * m.M + j) * 2 + 0] : m.h0[j];
+            const float h1 = tab ? (float)m.hill_tab[(set * m.M + j) * 2 + 1] : m.h1[j];
+            v = h0 + h1 / (1.0f + q);
         } else {
-            v = m.c[j];
+            v = m.n_sets > 1 ? (float)m.cprime_tab[set * m.M + j] : m.c[j];
 #pragma unroll 1
             for (int s = 0; s < m.N; ++s) {
                 if (m.folded[j][s]) continue;

@@ -110,3 +110,54 @@ def test_autotune_keeps_results(ssa):
     b.launch(s)
     s.synchronize()
     check(b, groups, 10.0, [10.0], "mixed_f16", "rn", False, 3, 100000)
+
+
+@pytest.mark.parametrize("prec,rnd,park", [("mixed_f16", "rn", 64), ("uniform_bf16", "sr", 200), ("fp64", "rn", 2)])
+def test_longest_first_batch_matches_oracle(ssa, prec, rnd, park):
+    """Longest-first scheduling forced on a batch: launch 1 parks every group's
+    trajectories at `park` events, the ordering kernels sort each group by
+    predicted remaining work with each set's own rate constants, launch 2
+    resumes them.  Direct launch and graph replay equal the oracle set by set
+    and the library counts five kernels per group plus two."""
+    groups = sweep_groups(ssa)
+    t_end, samples = 20.0, [10.0, 20.0]
+    api = [{k: v for k, v in G.items() if k != "dict"} for G in groups]
+    ssa.set_longest_first(2, park)
+    try:
+        b = ssa.Batch(api, t_end, samples, prec, rnd, seed=77, max_events=100000)
+    finally:
+        ssa.set_longest_first()
+    n0 = ssa.direct_kernel_launches()
+    b.launch()
+    torch.cuda.synchronize()
+    assert ssa.direct_kernel_launches() - n0 == 2 + 3 * len(groups)
+    check(b, groups, t_end, samples, prec, rnd, False, 77, 100000)
+    s = torch.cuda.Stream()
+    for _ in range(2):
+        for o in b.outputs:
+            o["snapshots"].fill_(-1)
+            o["n_events"].fill_(-1)
+        b.launch(s)
+        s.synchronize()
+        check(b, groups, t_end, samples, prec, rnd, False, 77, 100000)
+    # the autotuner times plain launches and keeps the split for the real ones
+    b.autotune(s)
+    b.launch(s)
+    s.synchronize()
+    check(b, groups, t_end, samples, prec, rnd, False, 77, 100000)
+
+
+def test_longest_first_batch_cap_below_parking_point(ssa):
+    """A parking point at or above the event cap parks nothing: one launch."""
+    groups = sweep_groups(ssa)
+    api = [{k: v for k, v in G.items() if k != "dict"} for G in groups]
+    ssa.set_longest_first(2, 5000)
+    try:
+        b = ssa.Batch(api, 20.0, [20.0], "mixed_f16", "rn", seed=9, max_events=5000)
+    finally:
+        ssa.set_longest_first()
+    n0 = ssa.direct_kernel_launches()
+    b.launch()
+    torch.cuda.synchronize()
+    assert ssa.direct_kernel_launches() - n0 == 1
+    check(b, groups, 20.0, [20.0], "mixed_f16", "rn", False, 9, 5000)

@@ -578,7 +578,7 @@ int ssa_hist_w1(const float *p, const float *q, int64_t rows, int bins, float *w
  * of n_draws independent draws from it, per row of p (device [rows][bins],
  * rows summing to 1): sum over b < bins-1 of sqrt(2 F(b)(1 - F(b)) / (pi n)),
  * the normal approximation of E|F_n(b) - F(b)| (F the cumulative law).  The
- * surrogate's judge uses it as the sampling noise of a small SSA ensemble.
+ * surrogate's check uses it as the sampling noise of a small SSA ensemble.
  * No paper counterpart.  Asynchronous.  Errors: SSA_EINVAL, SSA_ECUDA. */
 int ssa_hist_w1_noise(const float *p, int64_t rows, int bins, double n_draws, float *out, void *stream);
 

@@ -9,9 +9,9 @@ Workflow (host orchestration of the CUDA kernels in libssa_gb300.so):
   2. Training: the 4 -> 256 -> 256 -> 256 -> 128 GELU network on the tensor
      cores (tcgen05 GEMMs, bf16 operands, fp32 accumulation), AdamW with a
      cosine learning-rate schedule, cross-entropy against the histograms.
-  3. Serving: the network answers every query point, and the plain SSA judges
+  3. Serving: the network answers every query point, and the plain SSA checks
      it: each prediction is compared (Wasserstein-1, copies) with a small SSA
-     ensemble of the same point (JUDGE_TRAJ trajectories); a point whose
+     ensemble of the same point (CHECK_TRAJ trajectories); a point whose
      distance exceeds the 0.5-copy threshold plus that ensemble's expected
      sampling noise (ssa_hist_w1_noise) is re-simulated with FALLBACK_TRAJ
      trajectories and answered by the SSA instead.  What the network gains is
@@ -40,7 +40,7 @@ T_END = 200.0
 LOG_LO = np.log(np.array([0.05, 0.05, 5.0, 0.5]))
 LOG_HI = np.log(np.array([5.0, 5.0, 100.0, 2.0]))
 W1_THRESHOLD = 0.5
-JUDGE_TRAJ = 64         # SSA trajectories per point that judge a prediction
+CHECK_TRAJ = 64         # SSA trajectories per point that check a prediction
 FALLBACK_TRAJ = 1024    # SSA trajectories per point of a re-simulated (or SSA-only) answer
 
 
@@ -89,17 +89,17 @@ def train(net, feats, hists, steps, batch_size, lr_max=2e-3, lr_min=5e-5, weight
     return [(k * every, float(v)) for k, v in enumerate(losses.cpu().tolist())]
 
 
-def serve(net, query_params, seed, traj_offset, judge_traj=JUDGE_TRAJ, fallback_traj=FALLBACK_TRAJ):
-    """Answer query points with the network, judged by the SSA.
+def serve(net, query_params, seed, traj_offset, check_traj=CHECK_TRAJ, fallback_traj=FALLBACK_TRAJ):
+    """Answer query points with the network, checked by the SSA.
 
-    Returns (answers [n, 128] device, judge W1 [n], fallback mask [n] device,
+    Returns (answers [n, 128] device, check W1 [n], fallback mask [n] device,
     number of re-simulated points)."""
     import torch
     feats = torch.from_numpy(standardise(query_params)).cuda()
     q = net.predict(feats)
-    judge = simulate_histograms(query_params, judge_traj, seed=seed, traj_offset=traj_offset)
-    w1 = ssa.hist_w1(q, judge)
-    noise = ssa.hist_w1_noise(q, judge_traj)
+    check = simulate_histograms(query_params, check_traj, seed=seed, traj_offset=traj_offset)
+    w1 = ssa.hist_w1(q, check)
+    noise = ssa.hist_w1_noise(q, check_traj)
     fallback = w1 > W1_THRESHOLD + noise
     idx = torch.nonzero(fallback).flatten()
     answer = q
@@ -112,7 +112,7 @@ def serve(net, query_params, seed, traj_offset, judge_traj=JUDGE_TRAJ, fallback_
     return answer, w1, fallback, n_fb
 
 
-def run(n_train=2**16, traj_train=1024, n_query=2**14, judge_traj=JUDGE_TRAJ, fallback_traj=FALLBACK_TRAJ,
+def run(n_train=2**16, traj_train=1024, n_query=2**14, check_traj=CHECK_TRAJ, fallback_traj=FALLBACK_TRAJ,
         steps=6000, batch_size=1024, seed=2605):
     """The full surrogate configuration; returns a report dict."""
     import torch
@@ -138,13 +138,13 @@ def run(n_train=2**16, traj_train=1024, n_query=2**14, judge_traj=JUDGE_TRAJ, fa
     ent = -(h_train * torch.log(h_train.clamp_min(1e-30))).sum(dim=1).mean()
     report["target_entropy"] = float(ent)
     # 3. serving held-out points: the SSA alone (every point at FALLBACK_TRAJ
-    # trajectories) against the network judged by small SSA ensembles; both
+    # trajectories) against the network checked by small SSA ensembles; both
     # answers' accuracy against an independent SSA ensemble of each point
     qp = draw_parameters(n_query, seed + 1)
     feats_q = torch.from_numpy(standardise(qp)).cuda()
     # warm-up: one untimed pass of both paths on a few points (first uses of
     # the kernels and of the host-side selection of fallback points)
-    serve(net, qp[:256], seed + 5, 2**29, judge_traj, fallback_traj)
+    serve(net, qp[:256], seed + 5, 2**29, check_traj, fallback_traj)
     simulate_histograms(qp[:256], fallback_traj, seed=seed + 6, traj_offset=2**29)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -152,10 +152,10 @@ def run(n_train=2**16, traj_train=1024, n_query=2**14, judge_traj=JUDGE_TRAJ, fa
     torch.cuda.synchronize()
     ssa_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    answer, w1, fallback, n_fb = serve(net, qp, seed + 9, 2**30, judge_traj, fallback_traj)
+    answer, w1, fallback, n_fb = serve(net, qp, seed + 9, 2**30, check_traj, fallback_traj)
     torch.cuda.synchronize()
     serve_s = time.perf_counter() - t0
-    twin = simulate_histograms(qp, fallback_traj, seed=seed + 8, traj_offset=2**31)   # independent judge of both
+    twin = simulate_histograms(qp, fallback_traj, seed=seed + 8, traj_offset=2**31)   # independent reference for both
     t0 = time.perf_counter()
     reps = 20
     for _ in range(reps):
@@ -167,7 +167,7 @@ def run(n_train=2**16, traj_train=1024, n_query=2**14, judge_traj=JUDGE_TRAJ, fa
     w1_pred = ssa.hist_w1(net.predict(feats_q), twin).cpu().numpy()
     torch.cuda.synchronize()
     report.update({
-        "judge_traj": judge_traj, "fallback_traj": fallback_traj,
+        "check_traj": check_traj, "fallback_traj": fallback_traj,
         "ssa_only_s": ssa_s, "served_s": serve_s, "speedup_end_to_end": ssa_s / serve_s,
         "surrogate_predict_s": nn_s, "speedup_predict_only": ssa_s / nn_s,
         "fallback_fraction": n_fb / n_query,
@@ -175,7 +175,7 @@ def run(n_train=2**16, traj_train=1024, n_query=2**14, judge_traj=JUDGE_TRAJ, fa
         "w1_ssa_only_vs_twin_mean": float(w1_ssa.mean()), "w1_ssa_only_vs_twin_median": float(np.median(w1_ssa)),
         "w1_prediction_vs_twin_median": float(np.median(w1_pred)),
         "served_above_1_copy": float(np.mean(w1_ans > 1.0)), "ssa_only_above_1_copy": float(np.mean(w1_ssa > 1.0)),
-        "w1_judge_median": float(np.median(w1.cpu().numpy())),
+        "w1_check_median": float(np.median(w1.cpu().numpy())),
     })
     net.close()
     return report

@@ -171,7 +171,7 @@ def test_composition_bound_covers_fp32_and_catches_planted_mistakes():
 
 
 def test_expected_w1_noise_matches_monte_carlo():
-    """The judge's sampling-noise estimate against brute force: the mean W1
+    """The check's sampling-noise estimate against brute force: the mean W1
     between a law and many n-draw empirical histograms of it (Poisson and
     bimodal laws on 0..127, n = 64 and 1024) within 5%."""
     import scipy.stats

@@ -342,8 +342,9 @@ int ssa_tail_stats(int64_t *moved, int64_t *lock_timeouts, int64_t *resumed);
  * trajectory) with stream-ordered allocation and runs one plain launch if
  * that fails.  ssa_batch_create applies the setting in force when it is
  * called, per group, to that batch's launches: a group parks by the same
- * rule with its mean a0(x0) * t_end over its sets (the ordering uses each
- * set's own rate constants), the batch's scratch is part of its device
+ * rule with its mean a0(x0) * t_end over its sets, and in automatic mode
+ * also when that estimate differs by 4x or more between its sets (the
+ * ordering uses each set's own rate constants), the batch's scratch is part of its device
  * tables, and ssa_batch_launch then runs launch 1, the ordering kernels of
  * every parking group and launch 2 (all captured in its graph); the
  * autotuner times plain launches.  ssa_sweep_run_noalloc never splits.  Not

@@ -76,6 +76,7 @@ int g_longest_first = 1;
 int64_t g_park_events = 0;
 constexpr double kLongestFirstMinEvents = 4096.0;   // estimated events per trajectory
 constexpr int64_t kLongestFirstMinPerLane = 2;      // trajectories per resident lane
+constexpr double kLongestFirstMinSpread = 4.0;      // batches: largest / smallest estimate over the sets
 std::atomic<long long> g_direct_launches{0};        // kernels launched by launch_run
 
 }  // namespace
@@ -1042,6 +1043,7 @@ int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, 
     int64_t work = 0;
     bool compact = true;
     double est_events[ssa::kMaxGroups] = {0.0};
+    double est_spread[ssa::kMaxGroups] = {0.0};
     for (int g = 0; g < n_groups; ++g) {
         const ssa_batch_group &G = groups[g];
         if (!G.model) return fail(SSA_EINVAL, "group %d: model is NULL", g);
@@ -1071,8 +1073,9 @@ int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, 
         if (fam < 3) compact = false;
         work += items;
         bytes += group_tables(G.n_sets, G.model->M, G.model->N).total();
-        // mean estimated events per trajectory over the group's sets
-        double est = 0.0;
+        // mean and spread of the estimated events per trajectory over the
+        // group's sets
+        double est = 0.0, est_lo = 1e300, est_hi = 0.0;
         for (int64_t q = 0; q < G.n_sets; ++q) {
             ssa_model mq = *G.model;
             for (int j = 0; j < mq.M; ++j) {
@@ -1080,9 +1083,13 @@ int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, 
                 if (G.hill && mq.law[j] == SSA_LAW_HILL_REPRESSION)
                     for (int c = 0; c < 2; ++c) mq.hill[j][c] = G.hill[(q * mq.M + j) * 2 + c];
             }
-            est += estimated_events(mq, G.x0 + q * mq.N, normalise, t_end);
+            const double e = estimated_events(mq, G.x0 + q * mq.N, normalise, t_end);
+            est += e;
+            est_lo = std::min(est_lo, e);
+            est_hi = std::max(est_hi, e);
         }
         est_events[g] = est / (double)G.n_sets;
+        est_spread[g] = est_hi > 0.0 ? est_hi / std::max(est_lo, 1e-300) : 1.0;
     }
     // longest-first scheduling per group (as for single runs)
     int64_t park[ssa::kMaxGroups] = {0};
@@ -1095,7 +1102,10 @@ int ssa_batch_create(int n_groups, const ssa_batch_group *groups, double t_end, 
         for (int g = 0; g < n_groups && enough; ++g) {
             const int64_t items = groups[g].n_sets * groups[g].traj_per_set;
             if (items < 1) continue;
-            if (g_longest_first == 1 && !(est_events[g] >= kLongestFirstMinEvents)) continue;
+            // automatic: long trajectories, or sets whose estimated work spreads widely
+            if (g_longest_first == 1 && !(est_events[g] >= kLongestFirstMinEvents) &&
+                !(est_spread[g] >= kLongestFirstMinSpread))
+                continue;
             int64_t pe = g_park_events;
             if (pe <= 0) {
                 const double p = est_events[g] / 5.0;

@@ -55,11 +55,15 @@ def standardise(params):
 
 
 def simulate_histograms(params, traj_per_set, seed, traj_offset=0, precision="mixed_f16", rounding="rn",
-                        chunk_sets=8192, stream=None):
-    """Per-set mRNA histograms [n_sets, 128] (device) from SSA ensembles."""
+                        chunk_traj=2**23, stream=None):
+    """Per-set mRNA histograms [n_sets, 128] (device) from SSA ensembles, in
+    batched launches of at most chunk_traj trajectories (whole sets): small
+    ensembles per set go in one launch, which keeps every lane busy for
+    several trajectories."""
     import torch
     model = ssa.Model.from_dict(P.telegraph())
     n = params.shape[0]
+    chunk_sets = max(1, chunk_traj // max(1, traj_per_set))
     out = torch.empty((n, BINS), dtype=torch.float32, device="cuda")
     for a in range(0, n, chunk_sets):
         b = min(n, a + chunk_sets)

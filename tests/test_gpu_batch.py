@@ -161,3 +161,29 @@ def test_longest_first_batch_cap_below_parking_point(ssa):
     torch.cuda.synchronize()
     assert ssa.direct_kernel_launches() - n0 == 1
     check(b, groups, 20.0, [20.0], "mixed_f16", "rn", False, 9, 5000)
+
+
+def test_longest_first_full_family_batch(ssa):
+    """The full batch instantiation (birth-death, Schloegl normalised and a
+    general-kernel Hill network) with every group parked and resumed."""
+    bd, sch, gen = P.birth_death(), P.schlogl(), P.hill_self(1.0, 30.0, 2, 1.0)
+    groups = [
+        {"dict": sch, "model": ssa.Model.from_dict(sch), "x0": np.tile(P.schlogl_x0(sch), (2, 1)),
+         "rates": np.array([[3e-7, 1e-4, 1e-3, 3.5], [3.3e-7, 1e-4, 1e-3, 3.4]]), "traj_per_set": 24, "traj_offset": 5},
+        {"dict": bd, "model": ssa.Model.from_dict(bd), "x0": np.array([[0], [50]]), "traj_per_set": 70,
+         "traj_offset": 1000},
+        {"dict": gen, "model": ssa.Model.from_dict(gen), "x0": np.array([[0]]), "traj_per_set": 90,
+         "traj_offset": 3000},
+    ]
+    api = [{k: v for k, v in G.items() if k != "dict"} for G in groups]
+    for prec, rnd, park in [("mixed_f16", "sr", 16), ("uniform_f16", "rn", 100)]:
+        ssa.set_longest_first(2, park)
+        try:
+            b = ssa.Batch(api, 2.0, [1.0, 2.0], prec, rnd, normalise=True, seed=5, max_events=50000)
+        finally:
+            ssa.set_longest_first()
+        n0 = ssa.direct_kernel_launches()
+        b.launch()
+        torch.cuda.synchronize()
+        assert ssa.direct_kernel_launches() - n0 == 2 + 3 * len(groups)
+        check(b, groups, 2.0, [1.0, 2.0], prec, rnd, True, 5, 50000)

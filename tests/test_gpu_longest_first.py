@@ -53,6 +53,8 @@ CASES = {
     "dimer_fp64": (P.dimer(), P.dimer_x0(300), 4000, 5.0, P.even_samples(5.0, 4), False, 10**6, "fp64", "rn", 64),
     "birth_death_mixed_f16_rn": (P.birth_death(), [0], 30000, 30.0, P.even_samples(30.0, 6), False, 10**6,
                                  "mixed_f16", "rn", 2),
+    "hill_general_uniform_bf16_sr": (P.hill_self(1.0, 30.0, 2, 1.0), [0], 12000, 20.0, P.even_samples(20.0, 5),
+                                     False, 10**6, "uniform_bf16", "sr", 40),
 }
 
 _ORACLE = {}

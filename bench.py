@@ -1036,19 +1036,20 @@ def run_models(args, world, rank, local, workload):
     ssa.ensemble_run_host(model, n, x0, sp["t_end"], sp["samples"], MODES16[0][0], MODES16[0][1], False, SEED,
                           sp["cap"], 4, out=h[0].numpy(), status=h[1].numpy().view(np.uint32), n_events=h[2].numpy(),
                           t_final=h[3].numpy(), traj_offset=offset)
-    e2e_events, e2e_time, h2d, d2h = 0.0, 0.0, 0, 0
-    e2e_ms = {}
-    for prec, rnd in MODES16:
-        t1 = time.perf_counter()
-        ssa.ensemble_run_host(model, n, x0, sp["t_end"], sp["samples"], prec, rnd, False, SEED, sp["cap"], 4,
-                              out=h[0].numpy(), status=h[1].numpy().view(np.uint32), n_events=h[2].numpy(),
-                              t_final=h[3].numpy(), traj_offset=offset)
-        dt = time.perf_counter() - t1
-        e2e_time += dt
-        e2e_ms[f"{prec}:{rnd}"] = 1e3 * dt
-        e2e_events += float(h[2].numpy().sum())
-        h2d += x0.nbytes + np.asarray(sp["samples"]).nbytes
-        d2h += sum(v.numel() * v.element_size() for v in h)
+    e2e_events, e2e_time = 0.0, 0.0
+    h2d = len(MODES16) * (x0.nbytes + np.asarray(sp["samples"]).nbytes)          # per step
+    d2h = len(MODES16) * sum(v.numel() * v.element_size() for v in h)
+    e2e_ms = {f"{p}:{r}": [] for p, r in MODES16}
+    for _ in range(args.steps):                                  # the same steps as the device timing
+        for prec, rnd in MODES16:
+            t1 = time.perf_counter()
+            ssa.ensemble_run_host(model, n, x0, sp["t_end"], sp["samples"], prec, rnd, False, SEED, sp["cap"], 4,
+                                  out=h[0].numpy(), status=h[1].numpy().view(np.uint32), n_events=h[2].numpy(),
+                                  t_final=h[3].numpy(), traj_offset=offset)
+            dt = time.perf_counter() - t1
+            e2e_time += dt
+            e2e_ms[f"{prec}:{rnd}"].append(round(1e3 * dt, 2))
+            e2e_events += float(h[2].numpy().sum())
     e2e_time = max_over_ranks(world, e2e_time)
     e2e_events = sum_over_ranks(world, e2e_events)
     if rank != 0:
